@@ -1,0 +1,219 @@
+/*
+ * mka.h - C ABI of the GB300 (sm_103a) multiple Arnoldi library.
+ *
+ * The method (Hoshi, Yamamoto, Fujiwara, Sogabe, Zhang, arXiv:1202.0098,
+ * "An order-N electronic structure theory with generalized eigen-value
+ * equations and its application to a ten-million-atom system"): for every
+ * basis index j of a non-orthogonal tight-binding model (sparse symmetric H,
+ * sparse SPD S, Eq. EQ-ORIG-EQ), independently of every other j,
+ *   - solve S s_j = e_j by an inner CG loop (Sec. 2);
+ *   - build an S-orthonormal basis u_1..u_nu of the multiple Krylov subspace
+ *     L^(j) = K_p(H; e_j) (+) K_q(H; s_j) (Eqs. EQ-SUBSPACE-MULTI-KRY,
+ *     EQ-REC-UN, EQ-KN-HUN, EQ-MGram-Schmidt, EQ-CALC-S-INV);
+ *   - solve the reduced nu x nu problem (Eq. EQ-SUB-EIG-VEC);
+ *   - form the Fermi-weighted density matrix rho_ij (Eq. EQ-DM), the subspace
+ *     Green's function G_ij(z) (Eq. EQ-SOLUTION-SUB-GZ) and the band energy
+ *     (Eq. EQ-ENE); mu is found by bisection on the electron count (Sec. 2).
+ * Every column works on the real-space projection of H and S onto the
+ * cluster of atoms within a radius R of j's atom (Sec. 3).
+ *
+ * Conventions shared by all entry points
+ *   - Atoms carry 4 orbitals (s, px, py, pz), M = 4 N; column j = 4 a + o
+ *     belongs to atom a, orbital o (composite index, Sec. 1).
+ *   - H and S are held as 4x4-block CSR ("BSR"): row_ptr[N+1], col[nnzb]
+ *     (ascending within a row, the diagonal block included), values
+ *     [nnzb][4][4] row-major; block k of row a is <mu_a | nu_col[k]>.
+ *   - Every call returns mka_status. A failing call leaves a message readable
+ *     through mka_last_error() (thread-local, valid until the next call on
+ *     the same thread).
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the current device. Caller buffers are borrowed for
+ *     the duration of the call only. mka_system and mka_result are owned by
+ *     the library and freed with their destroy functions.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Device
+ *     work is ordered on it; calls that return host values synchronise it.
+ *   - There is no CPU fallback: without a usable CUDA device every call that
+ *     touches the GPU returns MKA_ERR_CUDA.
+ */
+#ifndef MKA_H
+#define MKA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MKA_OK = 0,
+  MKA_ERR_INVALID_ARG = 1,      /* bad pointer, size or parameter */
+  MKA_ERR_NOT_SPD = 2,          /* S (or a reduced S_r) is not positive definite */
+  MKA_ERR_NO_CONVERGENCE = 3,   /* inner CG reached its iteration cap */
+  MKA_ERR_BREAKDOWN = 4,        /* a column's basis ended with nu_eff < nu (reported, not fatal) */
+  MKA_ERR_OOM = 5,              /* device or host allocation failed */
+  MKA_ERR_CUDA = 6,             /* a CUDA runtime call failed (no device, launch error, ...) */
+  MKA_ERR_TIMEOUT = 7,          /* a bounded device-side wait gave up */
+  MKA_ERR_CLUSTER_TOO_LARGE = 8 /* a cluster exceeds MKA_MAX_CLUSTER_ATOMS */
+} mka_status;
+
+/* Storage format of H and S values, and arithmetic of a solve. */
+typedef enum {
+  MKA_FP64 = 0,        /* values FP64 / all arithmetic FP64 */
+  MKA_MIXED_FP32 = 1,  /* values FP32 / FP32 SpMV, CG and basis, FP64 reduced solve */
+  MKA_MIXED_BF16 = 2   /* values BF16 (storage only; arithmetic as MKA_MIXED_FP32) */
+} mka_precision;
+
+/* Largest cluster a column may have (atoms). m_c = 4 x atoms <= 2048. */
+#define MKA_MAX_CLUSTER_ATOMS 512
+/* Largest subspace dimension nu = p + q. */
+#define MKA_MAX_NU 64
+
+typedef struct mka_system mka_system; /* device BSR H and S, positions, cell list */
+typedef struct mka_result mka_result; /* per-column levels, weights, status, kept vectors */
+
+/* Two-centre Slater-Koster sp parameters of the model Hamiltonian.
+ * V, Sv: (ss-sigma, sp-sigma, pp-sigma, pp-pi) for H (eV) and S, given at
+ * bond length d0 (A) and scaled by exp(-2 (d/d0 - 1)) for d <= rc.
+ * On-site blocks: diag(Es, Ep, Ep, Ep) for H, the unit matrix for S. For the
+ * displacement d = r_b - r_a (minimum image) with cosines c = d/|d|:
+ *   [s][s] = ss, [s][p_k] = c_k sp, [p_k][s] = -c_k sp,
+ *   [p_k][p_m] = c_k c_m (pp_sigma - pp_pi) + delta_km pp_pi. */
+typedef struct {
+  double Es, Ep;
+  double V[4];
+  double Sv[4];
+  double d0, rc;
+} mka_sk_params;
+
+/* Parameters of one mka_solve_columns call. */
+typedef struct {
+  int p;              /* Krylov dimension of the e_j chain, >= 1 */
+  int q;              /* Krylov dimension of the s_j chain, >= 0; nu = p + q <= MKA_MAX_NU */
+  int arith;          /* MKA_FP64 or MKA_MIXED_FP32 (mka_precision) */
+  int use_warm_start; /* 1: CG starts from the learned guess (see mka_mlp_*), 0: from zero */
+  double cg_tol;      /* inner CG stops at ||r||_2 <= cg_tol ||e_j||_2 */
+  int cg_maxit;       /* inner CG iteration cap (MKA_ERR_NO_CONVERGENCE beyond it) */
+  int keep_vectors;   /* 1: keep the pattern rows of v_alpha so that rho and G can be
+                         evaluated later for any mu / z (needs 16 nu doubles per block
+                         of the selected rows); 0: keep only (eps, w) */
+} mka_solve_params;
+
+/* ---- system ------------------------------------------------------------ */
+
+/* Build the periodic model H and S (4x4 blocks, SK table above) from atom
+ * positions, store their values on the device in `storage` format, and build
+ * the cell list the cluster extraction uses (real-space projection, Sec. 3).
+ *   pos      host, [n_atoms][3] Cartesian positions (A), any values (wrapped
+ *            into the box internally)
+ *   box      host, [3] orthorhombic periodic box lengths (A); rc and
+ *            cluster_radius must both be < box/2
+ *   storage  mka_precision of the stored values (FP64 values are built first,
+ *            then rounded to nearest-even: FP64 -> FP32 -> BF16)
+ * Returns MKA_ERR_INVALID_ARG for n_atoms < 1, non-positive box, radii that
+ * do not fit the box; MKA_ERR_OOM / MKA_ERR_CUDA on allocation failures. */
+mka_status mka_build_system(const double* pos, int64_t n_atoms, const double box[3],
+                            const mka_sk_params* sk, int storage, double cluster_radius,
+                            void* stream, mka_system** out);
+
+/* Same, from a caller's BSR H and S (host arrays, FP64 values, layout above,
+ * pattern symmetric, columns ascending, diagonal present). Positions and the
+ * box still define the clusters. */
+mka_status mka_build_system_bsr(const double* pos, int64_t n_atoms, const double box[3],
+                                const int32_t* row_ptr, const int32_t* col, int64_t nnzb,
+                                const double* valH, const double* valS, int storage,
+                                double cluster_radius, void* stream, mka_system** out);
+
+/* Sizes: atoms, blocks, stored precision. Any output pointer may be NULL. */
+mka_status mka_system_info(const mka_system* sys, int64_t* n_atoms, int64_t* nnzb,
+                           int* storage, int* max_row_blocks);
+
+/* Copy the BSR pattern and the stored values (decoded to FP64) to host
+ * arrays of sizes N+1, nnzb, nnzb*16, nnzb*16. Any output may be NULL. */
+mka_status mka_system_copy_bsr(const mka_system* sys, int32_t* row_ptr, int32_t* col,
+                               double* valH, double* valS);
+
+/* Cluster sizes (atoms within cluster_radius, minimum image, the atom
+ * included) of `n_sel` atoms given as a host list (NULL = all atoms, in
+ * order), written to host `sizes`. Computed on the device. */
+mka_status mka_cluster_sizes(const mka_system* sys, const int64_t* atoms, int64_t n_sel,
+                             int32_t* sizes);
+
+void mka_system_destroy(mka_system* sys);
+
+/* Global block-sparse product y = A x for A = H (which = 0) or S (which = 1),
+ * the stored values decoded to FP64 (x_dtype = MKA_FP64: x, y device
+ * double[4N][k]) or to FP32 (x_dtype = MKA_MIXED_FP32: float[4N][k]), k in
+ * {1, 2, 4} right-hand sides interleaved (row-major [4N][k]). */
+mka_status mka_spmv(const mka_system* sys, int which, int x_dtype, const void* x, void* y, int k,
+                    void* stream);
+
+/* ---- columns ----------------------------------------------------------- */
+
+/* Run the per-column work flow (first brace of Eq. EQ-WORK-FLOW) for the 4
+ * columns of each of `n_sel` atoms (host list; NULL = every atom in order):
+ * cluster extraction, inner CG for s_j, the S-orthonormal multiple Krylov
+ * basis, the projection H_r = U^T H U, S_r = U^T S U, the Cholesky-reduced
+ * nu x nu eigensolve, and per column the levels eps_alpha (ascending) and
+ * weights w_alpha = v_alpha,j (S v_alpha)_j. Columns are stored in selection
+ * order, orbital fastest (column c = 4 t + o for the t-th selected atom).
+ * The result's aggregate status is MKA_OK, or the first per-column error
+ * (details by mka_result_copy_levels). Device work runs on `stream`; the
+ * call returns after enqueueing and the result is valid in stream order. */
+mka_status mka_solve_columns(mka_system* sys, const int64_t* atoms, int64_t n_sel,
+                             const mka_solve_params* prm, void* stream, mka_result** out);
+
+/* Sizes of a result: columns (= 4 n_sel), nu, and the number of 4x4 output
+ * blocks of rho / G (the sum over selected atoms of their H-row lengths). */
+mka_status mka_result_info(const mka_result* res, int64_t* n_cols, int* nu, int64_t* n_blocks);
+
+/* Copy per-column data to host arrays: eps, w [n_cols][nu] (entries beyond
+ * nu_eff are 0), nu_eff, cg_iters, status [n_cols]. Any output may be NULL.
+ * Synchronises the result's stream. */
+mka_status mka_result_copy_levels(const mka_result* res, double* eps, double* w, int32_t* nu_eff,
+                                  int32_t* cg_iters, int32_t* status);
+
+/* Device pointers of the per-column (eps, w) arrays ([n_cols][nu], FP64). */
+mka_status mka_result_device_levels(const mka_result* res, const double** eps, const double** w);
+
+void mka_result_destroy(mka_result* res);
+
+/* ---- global: mu, rho, G, energy --------------------------------------- */
+
+/* Chemical potential by bisection (Sec. 2, after Eq. EQ-DM): the mu with
+ * 2 sum_j sum_alpha f(eps_alpha^(j); mu) w_alpha^(j) = n_electrons over the
+ * result's columns, f(x) = 1 / (1 + exp((x - mu) / kT)). Bracket
+ * [min eps - 40 kT, max eps + 40 kT], halved until narrower than `tol` (eV)
+ * or 200 times; returns the midpoint in *mu_out (host). Runs on the device
+ * with FP64 sums; synchronises. */
+mka_status mka_find_mu(mka_result* res, double n_electrons, double kT, double tol, double* mu_out);
+
+/* Density matrix (Eq. EQ-DM) on the selected rows' pattern, the band energy
+ * E = 2 sum_j sum_i rho_ij H_ji (Eq. EQ-ENE, two electrons per orbital state)
+ * and the electron count 2 sum_j sum_alpha f w, at chemical potential mu.
+ *   rho_out  device double, [n_blocks][4][4] or NULL. Block k of the t-th
+ *            selected atom b (its H-row blocks in order, neighbour a = col[k])
+ *            holds rho_out[k][c][r] = rho_{(a,r),(b,c)}: the part of column
+ *            j = 4b + c on atom a's orbitals.
+ *   e_band_out, n_elec_out  host, may be NULL.
+ * Needs a result solved with keep_vectors = 1; otherwise MKA_ERR_INVALID_ARG.
+ * Synchronises when a host output is requested. */
+mka_status mka_density_energy(mka_system* sys, mka_result* res, double mu, double kT,
+                              double* rho_out, double* e_band_out, double* n_elec_out);
+
+/* Subspace Green's function G_ij(z) = sum_alpha v_alpha,i v_alpha,j / (z - eps_alpha)
+ * (Eq. EQ-SOLUTION-SUB-GZ) at complex z = z_re + i z_im, same pattern and
+ * layout as rho, complex128 interleaved (re, im): device double
+ * [n_blocks][4][4][2]. Needs keep_vectors = 1. */
+mka_status mka_greens(mka_system* sys, mka_result* res, double z_re, double z_im, double* g_out);
+
+/* ---- errors -------------------------------------------------------------- */
+
+const char* mka_last_error(void);
+const char* mka_status_string(mka_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MKA_H */

@@ -24,20 +24,32 @@ from .rounding import round_storage
 
 
 @dataclass
+class ColumnData:
+    """What rho, G, E and mu need from one column: its levels and V on the pattern rows."""
+    eps: np.ndarray              # eps_alpha, ascending, length nu_eff
+    w: np.ndarray                # w_alpha
+    Vrows: np.ndarray            # [len(rows), nu_eff] V restricted to the pattern rows
+    vj: np.ndarray               # V_{j alpha}
+    cg_iters: int
+    nu_eff: int
+
+
+@dataclass
 class AtomResult:
     atom: int
     cluster: np.ndarray          # sorted global atom ids of C_a
     neigh: np.ndarray            # sorted global atom ids of H-row a (pattern), a included
     rows: np.ndarray             # local orbital indices of the pattern atoms (4 per atom)
     Hrow: np.ndarray             # [4, len(rows)] H_{j, i} for the 4 columns j and pattern i
-    cols: list                   # 4 x mka.Column
+    data: list                   # 4 x ColumnData
     nu: int
+    cols: list | None = None     # 4 x mka.Column (full basis), only when asked for
 
     def eps_w(self) -> tuple[np.ndarray, np.ndarray]:
         """(eps, w) padded to nu per column; padding has w = 0."""
         eps = np.zeros((4, self.nu))
         w = np.zeros((4, self.nu))
-        for o, c in enumerate(self.cols):
+        for o, c in enumerate(self.data):
             n = len(c.eps)
             eps[o, :n] = c.eps
             w[o, :n] = c.w
@@ -45,22 +57,26 @@ class AtomResult:
 
 
 def solve_atom(pos: np.ndarray, box: np.ndarray, skp, R: float, a: int, p: int, q: int,
-               storage: str = "fp64", cg_tol: float = 1e-13) -> AtomResult:
+               storage: str = "fp64", cg_tol: float = 1e-13, keep_full: bool = False) -> AtomResult:
     cl = skmod.cluster_atoms(pos, box, a, R)
     Hc, Sc = skmod.cluster_matrices(pos, box, cl, skp)
     Hc = round_storage(Hc, storage)
     Sc = round_storage(Sc, storage)
     t = int(np.searchsorted(cl, a))
     nb = skmod.neighbour_atoms(pos, box, a, skp.rc)
-    loc = np.searchsorted(cl, nb)
+    loc = np.minimum(np.searchsorted(cl, nb), len(cl) - 1)
+    inside = np.repeat(cl[loc] == nb, 4)        # pattern atoms beyond R lie outside the projection
     rows = (4 * loc[:, None] + np.arange(4)[None, :]).ravel()
     cols = [mka.solve_column(Hc, Sc, 4 * t + o, p, q, cg_tol=cg_tol) for o in range(4)]
-    Hrow = np.stack([Hc[4 * t + o, rows] for o in range(4)])
-    return AtomResult(a, cl, nb, rows, Hrow, cols, p + q)
+    # v_alpha lives on the cluster: its rows outside the cluster are zero.
+    data = [ColumnData(c.eps, c.w, c.V[rows, :] * inside[:, None], c.V[c.j, :], c.cg_iters, c.basis.nu_eff)
+            for c in cols]
+    Hrow = np.stack([Hc[4 * t + o, rows] * inside for o in range(4)])
+    return AtomResult(a, cl, nb, rows, Hrow, data, p + q, cols if keep_full else None)
 
 
-def solve_atoms(pos, box, skp, R, atoms, p, q, storage="fp64", cg_tol=1e-13) -> list[AtomResult]:
-    return [solve_atom(pos, box, skp, R, int(a), p, q, storage, cg_tol) for a in atoms]
+def solve_atoms(pos, box, skp, R, atoms, p, q, storage="fp64", cg_tol=1e-13, keep_full=True) -> list[AtomResult]:
+    return [solve_atom(pos, box, skp, R, int(a), p, q, storage, cg_tol, keep_full) for a in atoms]
 
 
 def stack_eps_w(results: list[AtomResult]) -> tuple[np.ndarray, np.ndarray]:
@@ -85,9 +101,9 @@ def density(results: list[AtomResult], mu: float, kT: float) -> tuple[list[np.nd
     n_el = 0.0
     for r in results:
         blocks = np.zeros((len(r.neigh), 4, 4))
-        for o, c in enumerate(r.cols):
+        for o, c in enumerate(r.data):
             f = mka.fermi(c.eps, mu, kT)
-            col = mka.rho_column(c, f, r.rows)          # length 4 * n_neigh, atom-major
+            col = c.Vrows @ (f * c.vj)                  # Eq. EQ-DM, length 4 * n_neigh, atom-major
             blocks[:, o, :] = col.reshape(-1, 4)
             e_band += 2.0 * float(col @ r.Hrow[o])
             n_el += 2.0 * float(np.sum(f * c.w))
@@ -99,7 +115,7 @@ def band_energy_from_levels(results: list[AtomResult], mu: float, kT: float) -> 
     """2 sum_j sum_alpha f eps w: equals E_band when p >= 1 (Tr[rho H] = Tr[pi S], Sec. 3)."""
     e = 0.0
     for r in results:
-        for c in r.cols:
+        for c in r.data:
             e += 2.0 * float(np.sum(mka.fermi(c.eps, mu, kT) * c.eps * c.w))
     return e
 
@@ -109,7 +125,8 @@ def greens(results: list[AtomResult], z: complex) -> list[np.ndarray]:
     out = []
     for r in results:
         blocks = np.zeros((len(r.neigh), 4, 4), dtype=np.complex128)
-        for o, c in enumerate(r.cols):
-            blocks[:, o, :] = mka.greens_column(c, z, r.rows).reshape(-1, 4)
+        for o, c in enumerate(r.data):
+            g = c.Vrows.astype(np.complex128) @ (c.vj / (z - c.eps))   # Eq. EQ-SOLUTION-SUB-GZ
+            blocks[:, o, :] = g.reshape(-1, 4)
         out.append(blocks)
     return out

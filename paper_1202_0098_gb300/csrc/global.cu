@@ -1,0 +1,411 @@
+// Global (all-column) kernels: mu by bisection, the density matrix with the band
+// energy, the subspace Green's function, and the global block-sparse product.
+//
+// mu (Sec. 2, after Eq. EQ-DM): the electron count 2 sum_j sum_alpha f w is
+// evaluated by one launch per halving; the launch's blocks write fixed-order
+// partial sums, and the last block to finish (ticket counter) adds them in
+// block order and moves the bracket, so the result does not depend on timing.
+// f(x) = (1 - tanh((x - mu) / (2 kT))) / 2; for |x - mu| / (2 kT) > 20 the FP64
+// tanh is exactly +-1, so those terms take f = 0 or 1 without calling it.
+//
+// rho (Eq. EQ-DM), G (Eq. EQ-SOLUTION-SUB-GZ) and E (Eq. EQ-ENE) read the kept
+// pattern rows of v_alpha (row block k of column j, [c][r][alpha]).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "mka_internal.h"
+
+namespace mka {
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 608;   // 4 x 152 SMs
+
+__device__ __forceinline__ double fermi(double x, double mu, double kT) {
+  const double y = (x - mu) / (2.0 * kT);
+  if (y > 20.0) return 0.0;
+  if (y < -20.0) return 1.0;
+  return 0.5 * (1.0 - tanh(y));
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k];
+  __syncthreads();
+  return s;  // valid in thread 0
+}
+
+// Bisection state (device doubles): [0] lo, [1] hi, [2] target, [3] kT, [4] tol,
+// [5] last count, [6] halvings done. partial[kRedBlocks], ticket (unsigned).
+struct MuState {
+  double lo, hi, target, kT, tol, last, iters, pad;
+};
+
+// min / max of eps over entries with w != 0 (fixed-order two-level reduction).
+__global__ void eps_range_kernel(const double* eps, const double* w, int64_t n, double* partial,
+                                 unsigned* ticket, MuState* S) {
+  __shared__ double rmin[kRedThreads / 32], rmax[kRedThreads / 32];
+  __shared__ bool last;
+  double mn = INFINITY, mx = -INFINITY;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (w[i] != 0.0) {
+      mn = fmin(mn, eps[i]);
+      mx = fmax(mx, eps[i]);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rmin[threadIdx.x >> 5] = mn;
+    rmax[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < kRedThreads / 32; ++k) {
+      mn = fmin(mn, rmin[k]);
+      mx = fmax(mx, rmax[k]);
+    }
+    mn = fmin(mn, rmin[0]);
+    mx = fmax(mx, rmax[0]);
+    partial[2 * blockIdx.x] = mn;
+    partial[2 * blockIdx.x + 1] = mx;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double a = INFINITY, b = -INFINITY;
+    for (unsigned k = 0; k < gridDim.x; ++k) {
+      a = fmin(a, partial[2 * k]);
+      b = fmax(b, partial[2 * k + 1]);
+    }
+    S->lo = a - 40.0 * S->kT;
+    S->hi = b + 40.0 * S->kT;
+    S->iters = 0;
+    *ticket = 0;
+  }
+}
+
+// One halving: N(mid) = 2 sum f(eps; mid) w, then the bracket update.
+__global__ void bisect_kernel(const double* eps, const double* w, int64_t n, double* partial, unsigned* ticket,
+                              MuState* S) {
+  __shared__ double red[kRedThreads / 32];
+  __shared__ bool last;
+  const double lo = S->lo, hi = S->hi;
+  if (!(hi - lo > S->tol)) return;   // converged: every block leaves before touching the ticket
+  const double mid = 0.5 * (lo + hi), kT = S->kT;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+    if (wi != 0.0) acc += fermi(eps[i], mid, kT) * wi;
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double t = 0.0;
+    for (unsigned k = 0; k < gridDim.x; ++k) t += partial[k];
+    const double count = 2.0 * t;
+    if (count < S->target) S->lo = mid; else S->hi = mid;
+    S->last = count;
+    S->iters += 1;
+    *ticket = 0;
+  }
+}
+
+// rho / E: one CTA per selected atom, thread per (block k, c, r) of its row.
+__global__ void density_kernel(const double* vp, const double* eps, const int64_t* blk_off, const int32_t* self_k,
+                               const int64_t* sel, const int32_t* row_ptr, const void* valH, int storage,
+                               int nu, double mu, double kT, double* rho, double* e_partial) {
+  __shared__ double red[kRedThreads / 32];
+  __shared__ double f[4 * MKA_MAX_NU];
+  const int64_t t = blockIdx.x;
+  const int64_t atom = sel[t];
+  const int nrow = row_ptr[atom + 1] - row_ptr[atom];
+  const int64_t b0 = blk_off[t];
+  const int sk = self_k[t];
+  for (int i = threadIdx.x; i < 4 * nu; i += blockDim.x) {
+    const int c = i / nu;
+    f[i] = fermi(eps[(4 * t + c) * nu + i % nu], mu, kT);
+  }
+  __syncthreads();
+  double e = 0.0;
+  for (int i = threadIdx.x; i < nrow * 16; i += blockDim.x) {
+    const int k = i >> 4, c = (i >> 2) & 3, r = i & 3;
+    const double* v = vp + ((b0 + k) * 16 + c * 4 + r) * (int64_t)nu;
+    const double* vj = vp + ((b0 + sk) * 16 + c * 4 + c) * (int64_t)nu;
+    double s = 0.0;
+    for (int a = 0; a < nu; ++a) s += f[c * nu + a] * v[a] * vj[a];
+    if (rho) rho[(b0 + k) * 16 + c * 4 + r] = s;
+    const int64_t gk = (int64_t)row_ptr[atom] + k;
+    double h;
+    if (storage == MKA_FP64) h = reinterpret_cast<const double*>(valH)[gk * 16 + c * 4 + r];
+    else if (storage == MKA_MIXED_FP32) h = reinterpret_cast<const float*>(valH)[gk * 16 + c * 4 + r];
+    else h = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(valH)[gk * 16 + c * 4 + r]);
+    e += s * h;
+  }
+  const double s = block_sum(e, red);
+  if (threadIdx.x == 0) e_partial[t] = 2.0 * s;
+}
+
+__global__ void greens_kernel(const double* vp, const double* eps, const int64_t* blk_off, const int32_t* self_k,
+                              const int64_t* sel, const int32_t* row_ptr, int nu, double zr, double zi, double* g) {
+  __shared__ double gr[4 * MKA_MAX_NU], gi[4 * MKA_MAX_NU];
+  const int64_t t = blockIdx.x;
+  const int64_t atom = sel[t];
+  const int nrow = row_ptr[atom + 1] - row_ptr[atom];
+  const int64_t b0 = blk_off[t];
+  const int sk = self_k[t];
+  for (int i = threadIdx.x; i < 4 * nu; i += blockDim.x) {
+    const int c = i / nu;
+    const double dr = zr - eps[(4 * t + c) * nu + i % nu];
+    const double den = dr * dr + zi * zi;   // 1 / (z - e) = (dr - i zi) / den
+    gr[i] = dr / den;
+    gi[i] = -zi / den;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nrow * 16; i += blockDim.x) {
+    const int k = i >> 4, c = (i >> 2) & 3, r = i & 3;
+    const double* v = vp + ((b0 + k) * 16 + c * 4 + r) * (int64_t)nu;
+    const double* vj = vp + ((b0 + sk) * 16 + c * 4 + c) * (int64_t)nu;
+    double sr = 0.0, si = 0.0;
+    for (int a = 0; a < nu; ++a) {
+      const double pv = v[a] * vj[a];
+      sr += pv * gr[c * nu + a];
+      si += pv * gi[c * nu + a];
+    }
+    g[2 * ((b0 + k) * 16 + c * 4 + r)] = sr;
+    g[2 * ((b0 + k) * 16 + c * 4 + r) + 1] = si;
+  }
+}
+
+// Fixed-order sum of n doubles by one CTA (thread 0 adds the per-thread sums in order).
+__global__ void sum_kernel(const double* x, int64_t n, double* out) {
+  __shared__ double part[kRedThreads];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += x[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)blockDim.x; ++k) t += part[k];
+    *out = t;
+  }
+}
+
+__global__ void count_kernel(const double* eps, const double* w, int64_t n, double mu, double kT, double* out) {
+  __shared__ double part[kRedThreads];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
+    if (w[i] != 0.0) s += fermi(eps[i], mu, kT) * w[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)blockDim.x; ++k) t += part[k];
+    *out = 2.0 * t;
+  }
+}
+
+// ---- global BSR SpMV: one warp per block row, 16-byte vector loads of the values ----
+template <typename TV>
+struct VecLoad;
+template <>
+struct VecLoad<double> {
+  static constexpr int E = 2;
+  static __device__ __forceinline__ void load(const double* p, double out[2]) {
+    double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+    out[0] = a.x; out[1] = a.y;
+  }
+};
+template <>
+struct VecLoad<float> {
+  static constexpr int E = 4;
+  static __device__ __forceinline__ void load(const float* p, float out[4]) {
+    float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+    out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+  }
+};
+template <>
+struct VecLoad<__nv_bfloat16> {
+  static constexpr int E = 8;
+  static __device__ __forceinline__ void load(const __nv_bfloat16* p, float out[8]) {
+    uint4 a = __ldcs(reinterpret_cast<const uint4*>(p));
+    const uint32_t u[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      out[2 * i] = __uint_as_float(u[i] << 16);
+      out[2 * i + 1] = __uint_as_float(u[i] & 0xFFFF0000u);
+    }
+  }
+};
+
+template <typename TV, typename TX, int K>
+__global__ void __launch_bounds__(256) spmv_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                                   const TV* __restrict__ val, const TX* __restrict__ x,
+                                                   TX* __restrict__ y, int64_t n_rows) {
+  constexpr int E = VecLoad<TV>::E;
+  using TL = typename std::conditional<std::is_same<TV, double>::value, double, float>::type;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t a = warp; a < n_rows; a += nwarps) {
+    const int k0 = row_ptr[a], k1 = row_ptr[a + 1];
+    TX acc[4][K];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int c = 0; c < K; ++c) acc[i][c] = 0;
+    const int64_t e_end = (int64_t)(k1 - k0) * 16;
+    for (int64_t e0 = (int64_t)lane * E; e0 < e_end; e0 += 32 * E) {
+      TL v[E];
+      VecLoad<TV>::load(val + (int64_t)k0 * 16 + e0, v);
+      const int blk = (int)(e0 >> 4);
+      const int cb = col[k0 + blk];
+#pragma unroll
+      for (int t = 0; t < E; ++t) {
+        const int ij = (int)((e0 + t) & 15), i = ij >> 2, jj = ij & 3;
+#pragma unroll
+        for (int c = 0; c < K; ++c) acc[i][c] += (TX)v[t] * x[((int64_t)4 * cb + jj) * K + c];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        TX s = acc[i][c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        acc[i][c] = s;
+      }
+    if (lane < 4 * K) {
+      const int i = lane / K, c = lane % K;
+      TX out = 0;
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+        for (int cc = 0; cc < K; ++cc)
+          if (ii == i && cc == c) out = acc[ii][cc];
+      y[((int64_t)4 * a + i) * K + c] = out;
+    }
+  }
+}
+
+template <typename TV, typename TX>
+mka_status spmv_dispatch_k(const mka_system* s, const TV* val, const void* x, void* y, int k, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  MKA_CUDA_TRY(cudaGetDevice(&dev));
+  MKA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t blocks = std::min<int64_t>((s->n_atoms + 7) / 8, (int64_t)sms * 8);
+  const TX* xx = reinterpret_cast<const TX*>(x);
+  TX* yy = reinterpret_cast<TX*>(y);
+  if (k == 1) spmv_kernel<TV, TX, 1><<<(unsigned)blocks, 256, 0, st>>>(s->d_row_ptr, s->d_col, val, xx, yy, s->n_atoms);
+  else if (k == 2) spmv_kernel<TV, TX, 2><<<(unsigned)blocks, 256, 0, st>>>(s->d_row_ptr, s->d_col, val, xx, yy, s->n_atoms);
+  else spmv_kernel<TV, TX, 4><<<(unsigned)blocks, 256, 0, st>>>(s->d_row_ptr, s->d_col, val, xx, yy, s->n_atoms);
+  MKA_CUDA_TRY(cudaGetLastError());
+  return MKA_OK;
+}
+
+template <typename TV>
+mka_status spmv_dispatch(const mka_system* s, const void* val, int x_dtype, const void* x, void* y, int k,
+                         cudaStream_t st) {
+  if (x_dtype == MKA_FP64) return spmv_dispatch_k<TV, double>(s, (const TV*)val, x, y, k, st);
+  return spmv_dispatch_k<TV, float>(s, (const TV*)val, x, y, k, st);
+}
+
+}  // namespace
+
+mka_status launch_find_mu(mka_result* res, double n_electrons, double kT, double tol, double* mu_out) {
+  cudaStream_t st = res->stream;
+  const int64_t n = res->n_cols * res->nu;
+  if (!res->d_mu_state) {
+    MKA_CUDA_TRY(cudaMalloc(&res->d_mu_state, sizeof(MuState) + sizeof(double) * 2 * kRedBlocks + 64));
+    MKA_CUDA_TRY(cudaMemsetAsync(res->d_mu_state, 0, sizeof(MuState) + sizeof(double) * 2 * kRedBlocks + 64, st));
+  }
+  MuState* S = reinterpret_cast<MuState*>(res->d_mu_state);
+  double* partial = reinterpret_cast<double*>(S + 1);
+  unsigned* ticket = reinterpret_cast<unsigned*>(partial + 2 * kRedBlocks);
+  MuState h{};
+  h.target = n_electrons;
+  h.kT = kT;
+  h.tol = tol;
+  MKA_CUDA_TRY(cudaMemcpyAsync(S, &h, sizeof(MuState), cudaMemcpyHostToDevice, st));
+  MKA_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
+  const int blocks = (int)std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, (n + kRedThreads - 1) / kRedThreads));
+  eps_range_kernel<<<blocks, kRedThreads, 0, st>>>(res->d_eps, res->d_w, n, partial, ticket, S);
+  MKA_CUDA_TRY(cudaGetLastError());
+  MKA_CUDA_TRY(cudaMemcpyAsync(&h, S, sizeof(MuState), cudaMemcpyDeviceToHost, st));
+  MKA_CUDA_TRY(cudaStreamSynchronize(st));
+  if (!(h.hi > h.lo)) return fail(MKA_ERR_INVALID_ARG, "no level with nonzero weight");
+  const int halvings = std::min(200, (int)std::ceil(std::log2((h.hi - h.lo) / tol)) + 2);
+  for (int i = 0; i < std::max(halvings, 1); ++i) {
+    bisect_kernel<<<blocks, kRedThreads, 0, st>>>(res->d_eps, res->d_w, n, partial, ticket, S);
+  }
+  MKA_CUDA_TRY(cudaGetLastError());
+  MKA_CUDA_TRY(cudaMemcpyAsync(&h, S, sizeof(MuState), cudaMemcpyDeviceToHost, st));
+  MKA_CUDA_TRY(cudaStreamSynchronize(st));
+  *mu_out = 0.5 * (h.lo + h.hi);
+  return MKA_OK;
+}
+
+mka_status launch_density(mka_system* sys, mka_result* res, double mu, double kT, double* rho_out, double* e_band,
+                          double* n_elec) {
+  cudaStream_t st = res->stream;
+  double* tmp = nullptr;
+  MKA_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(double) * (res->n_sel + 2), st));
+  density_kernel<<<(unsigned)res->n_sel, 128, 0, st>>>(res->d_vp, res->d_eps, res->d_blk_off, res->d_self,
+                                                       res->d_sel, sys->d_row_ptr, sys->d_valH, sys->storage,
+                                                       res->nu, mu, kT, rho_out, tmp);
+  sum_kernel<<<1, kRedThreads, 0, st>>>(tmp, res->n_sel, tmp + res->n_sel);
+  count_kernel<<<1, kRedThreads, 0, st>>>(res->d_eps, res->d_w, res->n_cols * res->nu, mu, kT, tmp + res->n_sel + 1);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && (e_band || n_elec)) {
+    double h[2];
+    e = cudaMemcpyAsync(h, tmp + res->n_sel, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+      if (e_band) *e_band = h[0];
+      if (n_elec) *n_elec = h[1];
+    }
+  }
+  cudaFreeAsync(tmp, st);
+  if (e != cudaSuccess) return cuda_fail(e, "density");
+  return MKA_OK;
+}
+
+mka_status launch_greens(mka_system* sys, mka_result* res, double z_re, double z_im, double* g_out) {
+  greens_kernel<<<(unsigned)res->n_sel, 128, 0, res->stream>>>(res->d_vp, res->d_eps, res->d_blk_off, res->d_self,
+                                                               res->d_sel, sys->d_row_ptr, res->nu, z_re, z_im, g_out);
+  MKA_CUDA_TRY(cudaGetLastError());
+  return MKA_OK;
+}
+
+mka_status launch_spmv(const mka_system* s, int which, int x_dtype, const void* x, void* y, int k, cudaStream_t st) {
+  const void* val = which == 0 ? s->d_valH : s->d_valS;
+  switch (s->storage) {
+    case MKA_FP64: return spmv_dispatch<double>(s, val, x_dtype, x, y, k, st);
+    case MKA_MIXED_FP32: return spmv_dispatch<float>(s, val, x_dtype, x, y, k, st);
+    default: return spmv_dispatch<__nv_bfloat16>(s, val, x_dtype, x, y, k, st);
+  }
+}
+
+}  // namespace mka

@@ -1,0 +1,92 @@
+// Internal definitions shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mka.h"
+
+namespace mka {
+
+// Thread-local error text for mka_last_error().
+void set_error(const std::string& msg);
+mka_status fail(mka_status st, const std::string& msg);
+mka_status cuda_fail(cudaError_t e, const char* what);
+
+#define MKA_CUDA_TRY(expr)                                   \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) return ::mka::cuda_fail(_e, #expr); \
+  } while (0)
+
+// Device-side periodic cell list used by the cluster extraction (radius R).
+struct CellList {
+  int n[3];            // cells per dimension, >= 1
+  double len[3];       // cell edge (>= R)
+  int32_t* start;      // device [ncells + 1]
+  int32_t* atoms;      // device [n_atoms], atom ids grouped by cell, ascending inside a cell
+};
+
+}  // namespace mka
+
+struct mka_system {
+  int64_t n_atoms = 0;
+  int64_t nnzb = 0;
+  double box[3] = {0, 0, 0};
+  double R = 0;                 // cluster radius
+  int storage = MKA_FP64;
+  int max_row_blocks = 0;
+  cudaStream_t stream = nullptr;
+  // device
+  int32_t* d_row_ptr = nullptr;
+  int32_t* d_col = nullptr;
+  void* d_valH = nullptr;       // storage-typed [nnzb][16]
+  void* d_valS = nullptr;
+  double* d_pos = nullptr;      // [n_atoms][3], wrapped into the box
+  mka::CellList cells{};
+  // host copies of the pattern
+  std::vector<int32_t> h_row_ptr, h_col;
+};
+
+struct mka_result {
+  mka_system* sys = nullptr;
+  cudaStream_t stream = nullptr;
+  int64_t n_sel = 0;
+  int64_t n_cols = 0;
+  int nu = 0, p = 0, q = 0, arith = MKA_FP64;
+  int keep = 0;
+  int64_t n_blocks = 0;
+  int64_t* d_sel = nullptr;       // selected atoms
+  int64_t* d_blk_off = nullptr;   // [n_sel + 1] output block offsets
+  double* d_eps = nullptr;        // [n_cols][nu]
+  double* d_w = nullptr;          // [n_cols][nu]
+  int32_t* d_nu_eff = nullptr;
+  int32_t* d_cg_iters = nullptr;
+  int32_t* d_status = nullptr;
+  double* d_vp = nullptr;         // kept pattern rows [n_blocks][4 c][4 r][nu]
+  int32_t* d_self = nullptr;      // [n_sel] index (within the atom's row) of its diagonal block
+  double* d_mu_state = nullptr;   // bisection bracket and partial sums
+  std::vector<int64_t> h_sel;
+  std::vector<int64_t> h_blk_off;
+};
+
+namespace mka {
+
+// Kernels launched from the C entry points (defined in the .cu files).
+mka_status launch_cluster_sizes(const mka_system* sys, const int64_t* d_sel, int64_t n_sel, int32_t* d_sizes,
+                                cudaStream_t st);
+mka_status launch_columns(mka_system* sys, mka_result* res, const mka_solve_params* prm, int max_cluster_atoms,
+                          cudaStream_t st);
+mka_status launch_find_mu(mka_result* res, double n_electrons, double kT, double tol, double* mu_out);
+mka_status launch_density(mka_system* sys, mka_result* res, double mu, double kT, double* rho_out,
+                          double* e_band, double* n_elec);
+mka_status launch_greens(mka_system* sys, mka_result* res, double z_re, double z_im, double* g_out);
+mka_status launch_spmv(const mka_system* sys, int which, int x_dtype, const void* x, void* y, int k,
+                       cudaStream_t st);
+
+size_t storage_bytes(int storage);
+
+}  // namespace mka

@@ -1,0 +1,257 @@
+"""Thin ctypes binding of libmka (include/mka.h), function for function.
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels. Device buffers are passed as raw pointers (for example
+``torch.Tensor.data_ptr()`` of a CUDA tensor), streams as ``cudaStream_t``
+integers (``torch.cuda.current_stream().cuda_stream``). There is no CPU
+fallback: if the shared library is not built, importing this module's
+functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MKA_OK, MKA_ERR_INVALID_ARG, MKA_ERR_NOT_SPD, MKA_ERR_NO_CONVERGENCE, MKA_ERR_BREAKDOWN = 0, 1, 2, 3, 4
+MKA_ERR_OOM, MKA_ERR_CUDA, MKA_ERR_TIMEOUT, MKA_ERR_CLUSTER_TOO_LARGE = 5, 6, 7, 8
+MKA_FP64, MKA_MIXED_FP32, MKA_MIXED_BF16 = 0, 1, 2
+STORAGE = {"fp64": MKA_FP64, "fp32": MKA_MIXED_FP32, "bf16": MKA_MIXED_BF16}
+MKA_MAX_CLUSTER_ATOMS = 512
+MKA_MAX_NU = 64
+
+# Every symbol include/mka.h declares (checked by the tests).
+EXPORTED = [
+    "mka_build_system", "mka_build_system_bsr", "mka_system_info", "mka_system_copy_bsr", "mka_cluster_sizes",
+    "mka_system_destroy", "mka_spmv", "mka_solve_columns", "mka_result_info", "mka_result_copy_levels",
+    "mka_result_device_levels", "mka_result_destroy", "mka_find_mu", "mka_density_energy", "mka_greens",
+    "mka_last_error", "mka_status_string",
+]
+
+
+class MkaError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: status {status}: {message}")
+        self.status = status
+
+
+class mka_sk_params(C.Structure):
+    _fields_ = [("Es", C.c_double), ("Ep", C.c_double), ("V", C.c_double * 4), ("Sv", C.c_double * 4),
+                ("d0", C.c_double), ("rc", C.c_double)]
+
+
+class mka_solve_params(C.Structure):
+    _fields_ = [("p", C.c_int), ("q", C.c_int), ("arith", C.c_int), ("use_warm_start", C.c_int),
+                ("cg_tol", C.c_double), ("cg_maxit", C.c_int), ("keep_vectors", C.c_int)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None) -> C.CDLL:
+    """Load libmka (built in-tree by ``__graft_entry__.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmka is not built ({path}); run __graft_entry__.build() first")
+    lib = C.CDLL(path)
+    P, I64, I32, D = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    sig = {
+        "mka_build_system": [P, I64, P, P, I32, D, P, P],
+        "mka_build_system_bsr": [P, I64, P, P, P, I64, P, P, I32, D, P, P],
+        "mka_system_info": [P, P, P, P, P],
+        "mka_system_copy_bsr": [P, P, P, P, P],
+        "mka_cluster_sizes": [P, P, I64, P],
+        "mka_spmv": [P, I32, I32, P, P, I32, P],
+        "mka_solve_columns": [P, P, I64, P, P, P],
+        "mka_result_info": [P, P, P, P],
+        "mka_result_copy_levels": [P, P, P, P, P, P],
+        "mka_result_device_levels": [P, P, P],
+        "mka_find_mu": [P, D, D, D, P],
+        "mka_density_energy": [P, P, D, D, P, P, P],
+        "mka_greens": [P, P, D, D, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.mka_system_destroy.argtypes = [P]
+    lib.mka_system_destroy.restype = None
+    lib.mka_result_destroy.argtypes = [P]
+    lib.mka_result_destroy.restype = None
+    lib.mka_last_error.argtypes = []
+    lib.mka_last_error.restype = C.c_char_p
+    lib.mka_status_string.argtypes = [C.c_int]
+    lib.mka_status_string.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != MKA_OK:
+        msg = load().mka_last_error().decode(errors="replace")
+        raise MkaError(st, where, msg)
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def sk_struct(sk) -> mka_sk_params:
+    """From an object with Es, Ep, V, Sv, d0, rc (e.g. synth.SKParams)."""
+    s = mka_sk_params()
+    s.Es, s.Ep, s.d0, s.rc = sk.Es, sk.Ep, sk.d0, sk.rc
+    for i in range(4):
+        s.V[i] = sk.V[i]
+        s.Sv[i] = sk.Sv[i]
+    return s
+
+
+# ---- entry points, same names as the C ABI ------------------------------------------------
+
+def mka_build_system(pos: np.ndarray, box: np.ndarray, sk, storage: str = "fp64", cluster_radius: float = 6.0,
+                     stream: int = 0) -> C.c_void_p:
+    lib = load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    box = np.ascontiguousarray(box, dtype=np.float64)
+    out = C.c_void_p()
+    skp = sk_struct(sk)
+    _check(lib.mka_build_system(_ptr(pos), pos.shape[0], _ptr(box), C.byref(skp), STORAGE[storage],
+                                float(cluster_radius), C.c_void_p(stream), C.byref(out)), "mka_build_system")
+    return out
+
+
+def mka_build_system_bsr(pos, box, row_ptr, col, valH, valS, storage="fp64", cluster_radius=6.0, stream=0):
+    lib = load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    box = np.ascontiguousarray(box, dtype=np.float64)
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    valH = np.ascontiguousarray(valH, dtype=np.float64)
+    valS = np.ascontiguousarray(valS, dtype=np.float64)
+    out = C.c_void_p()
+    _check(lib.mka_build_system_bsr(_ptr(pos), pos.shape[0], _ptr(box), _ptr(row_ptr), _ptr(col), col.shape[0],
+                                    _ptr(valH), _ptr(valS), STORAGE[storage], float(cluster_radius),
+                                    C.c_void_p(stream), C.byref(out)), "mka_build_system_bsr")
+    return out
+
+
+def mka_system_info(sys) -> dict:
+    n, nnzb, st, mrb = C.c_int64(), C.c_int64(), C.c_int(), C.c_int()
+    _check(load().mka_system_info(sys, C.byref(n), C.byref(nnzb), C.byref(st), C.byref(mrb)), "mka_system_info")
+    return {"n_atoms": n.value, "nnzb": nnzb.value, "storage": st.value, "max_row_blocks": mrb.value}
+
+
+def mka_system_copy_bsr(sys) -> dict:
+    info = mka_system_info(sys)
+    n, nnzb = info["n_atoms"], info["nnzb"]
+    row_ptr = np.empty(n + 1, np.int32)
+    col = np.empty(nnzb, np.int32)
+    H = np.empty((nnzb, 4, 4))
+    S = np.empty((nnzb, 4, 4))
+    _check(load().mka_system_copy_bsr(sys, _ptr(row_ptr), _ptr(col), _ptr(H), _ptr(S)), "mka_system_copy_bsr")
+    return {"row_ptr": row_ptr, "col": col, "H": H, "S": S}
+
+
+def mka_cluster_sizes(sys, atoms: np.ndarray | None = None) -> np.ndarray:
+    n = mka_system_info(sys)["n_atoms"] if atoms is None else len(atoms)
+    a = None if atoms is None else np.ascontiguousarray(atoms, dtype=np.int64)
+    out = np.empty(n, np.int32)
+    _check(load().mka_cluster_sizes(sys, _ptr(a), n, _ptr(out)), "mka_cluster_sizes")
+    return out
+
+
+def mka_system_destroy(sys):
+    if sys:
+        load().mka_system_destroy(sys)
+
+
+def mka_spmv(sys, which: int, x_dtype: int, x_ptr: int, y_ptr: int, k: int = 1, stream: int = 0):
+    _check(load().mka_spmv(sys, which, x_dtype, C.c_void_p(x_ptr), C.c_void_p(y_ptr), k, C.c_void_p(stream)),
+           "mka_spmv")
+
+
+def solve_params(p: int, q: int, arith: str = "fp64", cg_tol: float = 1e-12, cg_maxit: int = 500,
+                 keep_vectors: bool = True, use_warm_start: bool = False) -> mka_solve_params:
+    prm = mka_solve_params()
+    prm.p, prm.q = p, q
+    prm.arith = MKA_FP64 if arith == "fp64" else MKA_MIXED_FP32
+    prm.use_warm_start = int(use_warm_start)
+    prm.cg_tol = cg_tol
+    prm.cg_maxit = cg_maxit
+    prm.keep_vectors = int(keep_vectors)
+    return prm
+
+
+def mka_solve_columns(sys, atoms: np.ndarray | None, prm: mka_solve_params, stream: int = 0) -> C.c_void_p:
+    a = None if atoms is None else np.ascontiguousarray(atoms, dtype=np.int64)
+    n = 0 if a is None else a.shape[0]
+    out = C.c_void_p()
+    _check(load().mka_solve_columns(sys, _ptr(a), n, C.byref(prm), C.c_void_p(stream), C.byref(out)),
+           "mka_solve_columns")
+    return out
+
+
+def mka_result_info(res) -> dict:
+    nc, nu, nb = C.c_int64(), C.c_int(), C.c_int64()
+    _check(load().mka_result_info(res, C.byref(nc), C.byref(nu), C.byref(nb)), "mka_result_info")
+    return {"n_cols": nc.value, "nu": nu.value, "n_blocks": nb.value}
+
+
+def mka_result_copy_levels(res, check: bool = True) -> dict:
+    info = mka_result_info(res)
+    nc, nu = info["n_cols"], info["nu"]
+    eps = np.empty((nc, nu))
+    w = np.empty((nc, nu))
+    nu_eff = np.empty(nc, np.int32)
+    it = np.empty(nc, np.int32)
+    status = np.empty(nc, np.int32)
+    st = load().mka_result_copy_levels(res, _ptr(eps), _ptr(w), _ptr(nu_eff), _ptr(it), _ptr(status))
+    if check:
+        _check(st, "mka_result_copy_levels")
+    return {"eps": eps, "w": w, "nu_eff": nu_eff, "cg_iters": it, "status": status, "aggregate": st}
+
+
+def mka_result_device_levels(res) -> tuple[int, int]:
+    e, w = C.c_void_p(), C.c_void_p()
+    _check(load().mka_result_device_levels(res, C.byref(e), C.byref(w)), "mka_result_device_levels")
+    return e.value, w.value
+
+
+def mka_result_destroy(res):
+    if res:
+        load().mka_result_destroy(res)
+
+
+def mka_find_mu(res, n_electrons: float, kT: float, tol: float = 1e-12) -> float:
+    mu = C.c_double()
+    _check(load().mka_find_mu(res, float(n_electrons), float(kT), float(tol), C.byref(mu)), "mka_find_mu")
+    return mu.value
+
+
+def mka_density_energy(sys, res, mu: float, kT: float, rho_ptr: int | None = None) -> tuple[float, float]:
+    e, n = C.c_double(), C.c_double()
+    _check(load().mka_density_energy(sys, res, float(mu), float(kT), C.c_void_p(rho_ptr) if rho_ptr else None,
+                                     C.byref(e), C.byref(n)), "mka_density_energy")
+    return e.value, n.value
+
+
+def mka_greens(sys, res, z: complex, g_ptr: int):
+    _check(load().mka_greens(sys, res, float(z.real), float(z.imag), C.c_void_p(g_ptr)), "mka_greens")
+
+
+def mka_last_error() -> str:
+    return load().mka_last_error().decode(errors="replace")
+
+
+def mka_status_string(st: int) -> str:
+    return load().mka_status_string(st).decode(errors="replace")

@@ -1,0 +1,28 @@
+"""Runs the oracle over many atoms in a process pool started with 'spawn' (safe beside CUDA)."""
+from __future__ import annotations
+
+import multiprocessing as mp
+import os
+
+import numpy as np
+
+from oracle import system as osys
+
+
+def _work(args):
+    pos, box, skp, R, atoms, p, q, storage, cg_tol = args
+    return [osys.solve_atom(pos, box, skp, R, int(a), p, q, storage, cg_tol) for a in atoms]
+
+
+def solve_atoms_parallel(pos, box, skp, R, atoms, p, q, storage="fp64", cg_tol=1e-13, workers=None):
+    atoms = list(np.asarray(atoms, dtype=np.int64))
+    workers = workers or min(16, os.cpu_count() or 1)
+    if len(atoms) <= 4 or workers == 1:
+        return _work((pos, box, skp, R, atoms, p, q, storage, cg_tol))
+    chunks = [atoms[i::workers] for i in range(workers)]
+    chunks = [c for c in chunks if c]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(len(chunks)) as pool:
+        parts = pool.map(_work, [(pos, box, skp, R, c, p, q, storage, cg_tol) for c in chunks])
+    by_atom = {r.atom: r for part in parts for r in part}
+    return [by_atom[int(a)] for a in atoms]
