@@ -207,6 +207,13 @@ mka_status mka_density_energy(mka_system* sys, mka_result* res, double mu, doubl
  * [n_blocks][4][4][2]. Needs keep_vectors = 1. */
 mka_status mka_greens(mka_system* sys, mka_result* res, double z_re, double z_im, double* g_out);
 
+/* ---- accounting ---------------------------------------------------------- */
+
+/* Number of CUDA kernels this library has launched since it was loaded (all
+ * threads, all devices). Lets a caller count the device launches of a timed
+ * region: read it before and after. */
+int64_t mka_kernel_launches(void);
+
 /* ---- errors -------------------------------------------------------------- */
 
 const char* mka_last_error(void);

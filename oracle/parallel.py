@@ -1,4 +1,8 @@
-"""Runs the oracle over many atoms in a process pool started with 'spawn' (safe beside CUDA)."""
+"""Oracle: many atoms at once in a process pool started with 'spawn'.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring). 'spawn' keeps the pool
+safe beside a process that already holds a CUDA context.
+"""
 from __future__ import annotations
 
 import multiprocessing as mp
@@ -6,7 +10,7 @@ import os
 
 import numpy as np
 
-from oracle import system as osys
+from . import system as osys
 
 
 def _work(args):

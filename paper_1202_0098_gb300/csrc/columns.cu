@@ -948,6 +948,7 @@ mka_status run_columns(mka_system* sys, mka_result* res, const mka_solve_params*
   A.scratch = scratch;
   A.work_counter = counter;
   kern<<<(unsigned)slots, kThreads, smem, st>>>(A);
+  count_launches();
   cudaError_t e = cudaGetLastError();
   cudaFreeAsync(scratch, st);
   cudaFreeAsync(counter, st);
@@ -966,6 +967,7 @@ mka_status launch_cluster_sizes(const mka_system* sys, const int64_t* d_sel, int
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((n_sel + 7) / 8, 152 * 16);
   cluster_size_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(A, d_sizes);
+  count_launches();
   MKA_CUDA_TRY(cudaGetLastError());
   return MKA_OK;
 }

@@ -321,6 +321,7 @@ mka_status spmv_dispatch_k(const mka_system* s, const TV* val, const void* x, vo
   if (k == 1) spmv_kernel<TV, TX, 1><<<(unsigned)blocks, 256, 0, st>>>(s->d_row_ptr, s->d_col, val, xx, yy, s->n_atoms);
   else if (k == 2) spmv_kernel<TV, TX, 2><<<(unsigned)blocks, 256, 0, st>>>(s->d_row_ptr, s->d_col, val, xx, yy, s->n_atoms);
   else spmv_kernel<TV, TX, 4><<<(unsigned)blocks, 256, 0, st>>>(s->d_row_ptr, s->d_col, val, xx, yy, s->n_atoms);
+  count_launches();
   MKA_CUDA_TRY(cudaGetLastError());
   return MKA_OK;
 }
@@ -352,6 +353,7 @@ mka_status launch_find_mu(mka_result* res, double n_electrons, double kT, double
   MKA_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
   const int blocks = (int)std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, (n + kRedThreads - 1) / kRedThreads));
   eps_range_kernel<<<blocks, kRedThreads, 0, st>>>(res->d_eps, res->d_w, n, partial, ticket, S);
+  count_launches();
   MKA_CUDA_TRY(cudaGetLastError());
   MKA_CUDA_TRY(cudaMemcpyAsync(&h, S, sizeof(MuState), cudaMemcpyDeviceToHost, st));
   MKA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -360,6 +362,7 @@ mka_status launch_find_mu(mka_result* res, double n_electrons, double kT, double
   for (int i = 0; i < std::max(halvings, 1); ++i) {
     bisect_kernel<<<blocks, kRedThreads, 0, st>>>(res->d_eps, res->d_w, n, partial, ticket, S);
   }
+  count_launches(std::max(halvings, 1));
   MKA_CUDA_TRY(cudaGetLastError());
   MKA_CUDA_TRY(cudaMemcpyAsync(&h, S, sizeof(MuState), cudaMemcpyDeviceToHost, st));
   MKA_CUDA_TRY(cudaStreamSynchronize(st));
@@ -377,6 +380,7 @@ mka_status launch_density(mka_system* sys, mka_result* res, double mu, double kT
                                                        res->nu, mu, kT, rho_out, tmp);
   sum_kernel<<<1, kRedThreads, 0, st>>>(tmp, res->n_sel, tmp + res->n_sel);
   count_kernel<<<1, kRedThreads, 0, st>>>(res->d_eps, res->d_w, res->n_cols * res->nu, mu, kT, tmp + res->n_sel + 1);
+  count_launches(3);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && (e_band || n_elec)) {
     double h[2];
@@ -395,6 +399,7 @@ mka_status launch_density(mka_system* sys, mka_result* res, double mu, double kT
 mka_status launch_greens(mka_system* sys, mka_result* res, double z_re, double z_im, double* g_out) {
   greens_kernel<<<(unsigned)res->n_sel, 128, 0, res->stream>>>(res->d_vp, res->d_eps, res->d_blk_off, res->d_self,
                                                                res->d_sel, sys->d_row_ptr, res->nu, z_re, z_im, g_out);
+  count_launches();
   MKA_CUDA_TRY(cudaGetLastError());
   return MKA_OK;
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -88,5 +89,9 @@ mka_status launch_spmv(const mka_system* sys, int which, int x_dtype, const void
                        cudaStream_t st);
 
 size_t storage_bytes(int storage);
+
+// Kernel launches of this library (mka_kernel_launches).
+extern std::atomic<int64_t> g_kernel_launches;
+inline void count_launches(int64_t n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 }  // namespace mka

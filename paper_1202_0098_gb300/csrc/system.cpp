@@ -20,6 +20,7 @@
 namespace mka {
 
 static thread_local std::string g_err;
+std::atomic<int64_t> g_kernel_launches{0};
 
 void set_error(const std::string& msg) { g_err = msg; }
 
@@ -218,6 +219,8 @@ using namespace mka;
 extern "C" {
 
 const char* mka_last_error(void) { return g_err.c_str(); }
+
+int64_t mka_kernel_launches(void) { return g_kernel_launches.load(); }
 
 const char* mka_status_string(mka_status s) {
   switch (s) {

@@ -28,7 +28,7 @@ EXPORTED = [
     "mka_build_system", "mka_build_system_bsr", "mka_system_info", "mka_system_copy_bsr", "mka_cluster_sizes",
     "mka_system_destroy", "mka_spmv", "mka_solve_columns", "mka_result_info", "mka_result_copy_levels",
     "mka_result_device_levels", "mka_result_destroy", "mka_find_mu", "mka_density_energy", "mka_greens",
-    "mka_last_error", "mka_status_string",
+    "mka_kernel_launches", "mka_last_error", "mka_status_string",
 ]
 
 
@@ -88,6 +88,8 @@ def load(path: str | None = None) -> C.CDLL:
     lib.mka_system_destroy.restype = None
     lib.mka_result_destroy.argtypes = [P]
     lib.mka_result_destroy.restype = None
+    lib.mka_kernel_launches.argtypes = []
+    lib.mka_kernel_launches.restype = C.c_int64
     lib.mka_last_error.argtypes = []
     lib.mka_last_error.restype = C.c_char_p
     lib.mka_status_string.argtypes = [C.c_int]
@@ -247,6 +249,10 @@ def mka_density_energy(sys, res, mu: float, kT: float, rho_ptr: int | None = Non
 
 def mka_greens(sys, res, z: complex, g_ptr: int):
     _check(load().mka_greens(sys, res, float(z.real), float(z.imag), C.c_void_p(g_ptr)), "mka_greens")
+
+
+def mka_kernel_launches() -> int:
+    return int(load().mka_kernel_launches())
 
 
 def mka_last_error() -> str:

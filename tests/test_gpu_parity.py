@@ -10,7 +10,7 @@ import pytest
 from oracle import sk as osk, system as osys
 from oracle.rounding import round_storage
 from synth import SK_CARBON_LIKE, WORKLOADS, lattice_positions, workload_positions, sample_atoms
-from tests.oracle_runs import solve_atoms_parallel
+from oracle.parallel import solve_atoms_parallel
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
