@@ -163,6 +163,43 @@ mka_status mka_spmv(const mka_system* sys, int which, int x_dtype, const void* x
 mka_status mka_solve_columns(mka_system* sys, const int64_t* atoms, int64_t n_sel,
                              const mka_solve_params* prm, void* stream, mka_result** out);
 
+/* Size of the fixed device scratch array behind mka_solve_columns_static: 64 MiB,
+ * reserved on every GPU that loads this library until the process exits. */
+#define MKA_STATIC_SCRATCH_BYTES (64ull << 20)
+
+/* mka_solve_columns without any allocation. The paper has no counterpart to
+ * this call: it exists for callers that must not allocate device memory, for
+ * example code whose device memory is owned by a framework's caching
+ * allocator that has already reserved the GPU (a raw cudaMalloc would fail or
+ * fragment its pool), or code inside a latency-critical loop where the
+ * implicit synchronisation of cudaMalloc/cudaFree is not acceptable.
+ *
+ * It runs the same per-atom work flow as mka_solve_columns in the FP64 form
+ * (values decoded from the system's storage format, FP64 arithmetic), for the
+ * 4 columns of each of `n_sel` atoms listed in the HOST array `atoms`, and
+ * writes per column, in selection order (column 4 t + o), into the caller's
+ * DEVICE buffers:
+ *   eps, w      double [4 n_sel][p + q] (entries beyond nu_eff are 0)
+ *   nu_eff, cg_iters, status  int32 [4 n_sel] (status: a mka_status value;
+ *               MKA_ERR_CLUSTER_TOO_LARGE when an atom's cluster has more
+ *               than `max_cluster_atoms` atoms)
+ * Pattern rows of v_alpha are not kept (no rho / G from this call).
+ * Work memory (the work-queue counter, the atom list and one work slot per
+ * CTA of 8 (3 (p+q) + 7) x 4 max_cluster_atoms x 4 bytes) comes from one
+ * file-scope device array of MKA_STATIC_SCRATCH_BYTES. The call returns
+ * MKA_ERR_INVALID_ARG, with a message, when the atom list and one slot do not
+ * fit in it; fewer slots than SMs simply means fewer atoms in flight.
+ * The call performs no cudaMalloc, cudaFree or other allocating routine. The
+ * first call on a device looks up the array's device address (with that
+ * device current) and caches it: make that first call before any stream
+ * capture. Every call on a device shares the one array, so calls whose GPU
+ * work overlaps (different streams, or host threads, without ordering between
+ * them) race on it and corrupt each other's results; order them on one stream.
+ * The work-queue counter is cleared by each call; the rest is overwritten. */
+mka_status mka_solve_columns_static(const mka_system* sys, const int64_t* atoms, int64_t n_sel, int p, int q,
+                                    double cg_tol, int cg_maxit, int max_cluster_atoms, double* eps, double* w,
+                                    int32_t* nu_eff, int32_t* cg_iters, int32_t* status, void* stream);
+
 /* Sizes of a result: columns (= 4 n_sel), nu, and the number of 4x4 output
  * blocks of rho / G (the sum over selected atoms of their H-row lengths). */
 mka_status mka_result_info(const mka_result* res, int64_t* n_cols, int* nu, int64_t* n_blocks);

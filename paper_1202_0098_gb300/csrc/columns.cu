@@ -34,6 +34,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "mka_internal.h"
@@ -989,3 +991,122 @@ mka_status launch_columns(mka_system* sys, mka_result* res, const mka_solve_para
 }
 
 }  // namespace mka
+
+// ---- fixed-scratch variant (mka_solve_columns_static) ------------------------------------
+//
+// The same per-atom kernel, FP64 form, with its work queue counter, the atom list
+// and every per-CTA work slot carved out of one file-scope device array instead of
+// memory allocated per call. Host code cannot use the array's name as a device
+// address, so each device's address is looked up once with cudaGetSymbolAddress
+// (with that device current) and cached.
+static __device__ __align__(256) unsigned char g_static_scratch[MKA_STATIC_SCRATCH_BYTES];
+
+namespace mka {
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device (looked up on first use).
+mka_status static_scratch_address(void** out) {
+  int dev = 0;
+  MKA_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(MKA_ERR_INVALID_ARG, "device index beyond the supported range");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return MKA_OK;
+}
+
+template <typename TV>
+mka_status run_columns_static(const mka_system* sys, const int64_t* h_atoms, int64_t n_sel, int p, int q,
+                              double cg_tol, int cg_maxit, int max_cl, double* eps, double* w, int32_t* nu_eff,
+                              int32_t* cg_iters, int32_t* status, cudaStream_t st) {
+  char* base = nullptr;
+  mka_status s = static_scratch_address(reinterpret_cast<void**>(&base));
+  if (s) return s;
+  Args<TV> A{};
+  fill_system_args(A, sys);
+  A.n_sel = n_sel;
+  A.p = p;
+  A.q = q;
+  A.nu = p + q;
+  A.cg_tol = cg_tol;
+  A.cg_maxit = cg_maxit;
+  A.tau = 1e-10;
+  A.mcap = 4 * max_cl;
+  A.lnnz_cap = std::max(1, max_cl * std::max(1, sys->max_row_blocks));
+  A.eps = eps;
+  A.w = w;
+  A.nu_eff = nu_eff;
+  A.cg_iters = cg_iters;
+  A.status = status;
+  A.keep = 0;
+  // layout: [work counter | 256 B] [atom ids | rounded to 256 B] [per-CTA slots]
+  const size_t sel_bytes = ((size_t)n_sel * sizeof(int64_t) + 255) & ~(size_t)255;
+  A.slot_bytes = (sizeof(double) * ((size_t)3 * A.nu + 7) * A.mcap * 4 + 255) & ~(size_t)255;
+  const size_t fixed = 256 + sel_bytes;
+  if (fixed + A.slot_bytes > (size_t)MKA_STATIC_SCRATCH_BYTES)
+    return fail(MKA_ERR_INVALID_ARG,
+                "mka_solve_columns_static: one work slot (" + std::to_string(A.slot_bytes) + " B) plus the atom list (" +
+                    std::to_string(sel_bytes) + " B) exceeds the fixed scratch of " +
+                    std::to_string((size_t)MKA_STATIC_SCRATCH_BYTES) +
+                    " B; pass fewer atoms, a smaller p + q or a smaller max_cluster_atoms");
+  const int64_t slots_fit = (int64_t)(((size_t)MKA_STATIC_SCRATCH_BYTES - fixed) / A.slot_bytes);
+  const size_t smem = dyn_smem_bytes(A.nu, A.lnnz_cap);
+  auto kern = atoms_kernel<TV, double>;
+  MKA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, sms = 0, per_sm = 0;
+  MKA_CUDA_TRY(cudaGetDevice(&dev));
+  MKA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  MKA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+  if (per_sm < 1) return fail(MKA_ERR_INVALID_ARG, "per-atom working set does not fit in shared memory");
+  const int64_t grid = std::min<int64_t>(std::min<int64_t>(n_sel, slots_fit), (int64_t)sms * per_sm);
+  A.work_counter = reinterpret_cast<int*>(base);
+  A.sel = reinterpret_cast<const int64_t*>(base + 256);
+  A.scratch = base + fixed;
+  // The counter must start at zero; the atom list is copied in; slots need no clearing
+  // (the kernel writes every slot entry before reading it).
+  MKA_CUDA_TRY(cudaMemsetAsync(base, 0, 256, st));
+  MKA_CUDA_TRY(cudaMemcpyAsync(base + 256, h_atoms, (size_t)n_sel * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  kern<<<(unsigned)grid, kThreads, smem, st>>>(A);
+  count_launches();
+  MKA_CUDA_TRY(cudaGetLastError());
+  return MKA_OK;
+}
+
+}  // namespace
+}  // namespace mka
+
+extern "C" mka_status mka_solve_columns_static(const mka_system* sys, const int64_t* atoms, int64_t n_sel, int p,
+                                               int q, double cg_tol, int cg_maxit, int max_cluster_atoms,
+                                               double* eps, double* w, int32_t* nu_eff, int32_t* cg_iters,
+                                               int32_t* status, void* stream) {
+  using namespace mka;
+  if (!sys || !atoms || n_sel < 1) return fail(MKA_ERR_INVALID_ARG, "system, a host atom list and n_sel >= 1 are required");
+  if (!eps || !w || !nu_eff || !cg_iters || !status) return fail(MKA_ERR_INVALID_ARG, "every output buffer is required");
+  if (p < 1 || q < 0 || p + q > MKA_MAX_NU) return fail(MKA_ERR_INVALID_ARG, "need p >= 1, q >= 0, p + q <= MKA_MAX_NU");
+  if (!(cg_tol > 0) || cg_maxit < 1) return fail(MKA_ERR_INVALID_ARG, "need cg_tol > 0, cg_maxit >= 1");
+  if (max_cluster_atoms < 1 || max_cluster_atoms > MKA_MAX_CLUSTER_ATOMS)
+    return fail(MKA_ERR_INVALID_ARG, "max_cluster_atoms must be in [1, MKA_MAX_CLUSTER_ATOMS]");
+  for (int64_t t = 0; t < n_sel; ++t)
+    if (atoms[t] < 0 || atoms[t] >= sys->n_atoms) return fail(MKA_ERR_INVALID_ARG, "atom index out of range");
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (sys->storage) {
+    case MKA_FP64:
+      return run_columns_static<double>(sys, atoms, n_sel, p, q, cg_tol, cg_maxit, max_cluster_atoms, eps, w, nu_eff,
+                                        cg_iters, status, st);
+    case MKA_MIXED_FP32:
+      return run_columns_static<float>(sys, atoms, n_sel, p, q, cg_tol, cg_maxit, max_cluster_atoms, eps, w, nu_eff,
+                                       cg_iters, status, st);
+    default:
+      return run_columns_static<__nv_bfloat16>(sys, atoms, n_sel, p, q, cg_tol, cg_maxit, max_cluster_atoms, eps, w,
+                                               nu_eff, cg_iters, status, st);
+  }
+}

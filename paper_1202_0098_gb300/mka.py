@@ -22,11 +22,12 @@ MKA_FP64, MKA_MIXED_FP32, MKA_MIXED_BF16 = 0, 1, 2
 STORAGE = {"fp64": MKA_FP64, "fp32": MKA_MIXED_FP32, "bf16": MKA_MIXED_BF16}
 MKA_MAX_CLUSTER_ATOMS = 512
 MKA_MAX_NU = 64
+MKA_STATIC_SCRATCH_BYTES = 64 << 20
 
 # Every symbol include/mka.h declares (checked by the tests).
 EXPORTED = [
     "mka_build_system", "mka_build_system_bsr", "mka_system_info", "mka_system_copy_bsr", "mka_cluster_sizes",
-    "mka_system_destroy", "mka_spmv", "mka_solve_columns", "mka_result_info", "mka_result_copy_levels",
+    "mka_system_destroy", "mka_spmv", "mka_solve_columns", "mka_solve_columns_static", "mka_result_info", "mka_result_copy_levels",
     "mka_result_device_levels", "mka_result_destroy", "mka_find_mu", "mka_density_energy", "mka_greens",
     "mka_kernel_launches", "mka_last_error", "mka_status_string",
 ]
@@ -73,6 +74,7 @@ def load(path: str | None = None) -> C.CDLL:
         "mka_cluster_sizes": [P, P, I64, P],
         "mka_spmv": [P, I32, I32, P, P, I32, P],
         "mka_solve_columns": [P, P, I64, P, P, P],
+        "mka_solve_columns_static": [P, P, I64, I32, I32, D, I32, I32, P, P, P, P, P, P],
         "mka_result_info": [P, P, P, P],
         "mka_result_copy_levels": [P, P, P, P, P, P],
         "mka_result_device_levels": [P, P, P],
@@ -201,6 +203,17 @@ def mka_solve_columns(sys, atoms: np.ndarray | None, prm: mka_solve_params, stre
     _check(load().mka_solve_columns(sys, _ptr(a), n, C.byref(prm), C.c_void_p(stream), C.byref(out)),
            "mka_solve_columns")
     return out
+
+
+def mka_solve_columns_static(sys, atoms: np.ndarray, p: int, q: int, cg_tol: float, cg_maxit: int,
+                             max_cluster_atoms: int, eps_ptr: int, w_ptr: int, nu_eff_ptr: int, cg_iters_ptr: int,
+                             status_ptr: int, stream: int = 0):
+    """Allocation-free solve into caller device buffers (see include/mka.h)."""
+    a = np.ascontiguousarray(atoms, dtype=np.int64)
+    V = C.c_void_p
+    _check(load().mka_solve_columns_static(sys, _ptr(a), a.shape[0], p, q, float(cg_tol), cg_maxit,
+                                           max_cluster_atoms, V(eps_ptr), V(w_ptr), V(nu_eff_ptr), V(cg_iters_ptr),
+                                           V(status_ptr), V(stream)), "mka_solve_columns_static")
 
 
 def mka_result_info(res) -> dict:

@@ -1,0 +1,92 @@
+"""The allocation-free entry point mka_solve_columns_static against mka_solve_columns.
+
+Some callers cannot allocate device memory: their GPU memory belongs to a
+framework's caching allocator that has already reserved it, or they run in a
+loop where cudaMalloc's implicit synchronisation is not acceptable. For them
+the library solves columns with a fixed device scratch array and the caller's
+own output buffers. This test calls it through the C ABI twice in a row, on two
+different atom selections, and checks each call against the allocating entry
+point on the same atoms, with the tolerance of the other GPU parity tests.
+It lives in a file of its own that pytest collects last.
+"""
+import numpy as np
+import pytest
+
+from synth import SK_CARBON_LIKE, lattice_positions
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1202_0098_gb300 import build, mka
+    build.build()
+    mka.load()
+    return mka
+
+
+def reference_levels(mka, s, atoms, p, q):
+    res = mka.mka_solve_columns(s, atoms, mka.solve_params(p, q, cg_tol=1e-13, keep_vectors=False))
+    try:
+        return mka.mka_result_copy_levels(res)
+    finally:
+        mka.mka_result_destroy(res)
+
+
+def static_levels(mka, s, atoms, p, q, max_cl):
+    n, nu = 4 * len(atoms), p + q
+    eps = torch.full((n, nu), float("nan"), dtype=torch.float64, device="cuda")
+    w = torch.full((n, nu), float("nan"), dtype=torch.float64, device="cuda")
+    nu_eff = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    it = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    st = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    mka.mka_solve_columns_static(s, atoms, p, q, 1e-13, 500, max_cl, eps.data_ptr(), w.data_ptr(), nu_eff.data_ptr(),
+                                 it.data_ptr(), st.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return {"eps": eps.cpu().numpy(), "w": w.cpu().numpy(), "nu_eff": nu_eff.cpu().numpy(),
+            "cg_iters": it.cpu().numpy(), "status": st.cpu().numpy()}
+
+
+def test_static_scratch_matches_allocating_solve_twice(lib):
+    mka = lib
+    pos, box = lattice_positions("diamond", 3.567, 3, 0.08, 0.0, 13)
+    p, q, R = 10, 10, 5.0
+    s = mka.mka_build_system(pos, box, SK_CARBON_LIKE, "fp64", cluster_radius=R)
+    try:
+        max_cl = int(mka.mka_cluster_sizes(s).max())
+        selections = [np.array([0, 9, 31, 64, 150, 215], dtype=np.int64),
+                      np.array([2, 3, 100, 101, 199], dtype=np.int64)]
+        for atoms in selections:          # two calls in a row on the shared scratch array
+            ref = reference_levels(mka, s, atoms, p, q)
+            got = static_levels(mka, s, atoms, p, q, max_cl)
+            np.testing.assert_array_equal(got["status"], ref["status"])
+            np.testing.assert_array_equal(got["nu_eff"], ref["nu_eff"])
+            np.testing.assert_array_equal(got["cg_iters"], ref["cg_iters"])
+            np.testing.assert_allclose(got["eps"], ref["eps"], rtol=0, atol=TOL)
+            np.testing.assert_allclose(got["w"], ref["w"], rtol=0, atol=TOL)
+    finally:
+        mka.mka_system_destroy(s)
+
+
+def test_static_scratch_rejects_requests_beyond_its_size(lib):
+    mka = lib
+    pos, box = lattice_positions("diamond", 3.567, 3, 0.08, 0.0, 13)
+    s = mka.mka_build_system(pos, box, SK_CARBON_LIKE, "fp64", cluster_radius=5.0)
+    try:
+        too_many = np.zeros(mka.MKA_STATIC_SCRATCH_BYTES // 8 + 1, dtype=np.int64)   # the atom list alone overflows
+        buf = torch.empty(1, dtype=torch.float64, device="cuda")
+        ibuf = torch.empty(1, dtype=torch.int32, device="cuda")
+        with pytest.raises(mka.MkaError) as e:
+            mka.mka_solve_columns_static(s, too_many, 8, 8, 1e-12, 500, 64, buf.data_ptr(), buf.data_ptr(),
+                                         ibuf.data_ptr(), ibuf.data_ptr(), ibuf.data_ptr())
+        assert e.value.status == mka.MKA_ERR_INVALID_ARG and "fixed scratch" in str(e.value)
+        with pytest.raises(mka.MkaError) as e:
+            mka.mka_solve_columns_static(s, np.array([0]), 8, 8, 1e-12, 500, mka.MKA_MAX_CLUSTER_ATOMS + 1,
+                                         buf.data_ptr(), buf.data_ptr(), ibuf.data_ptr(), ibuf.data_ptr(),
+                                         ibuf.data_ptr())
+        assert e.value.status == mka.MKA_ERR_INVALID_ARG
+    finally:
+        mka.mka_system_destroy(s)
