@@ -210,7 +210,8 @@ def main():
     t_build = time.perf_counter() - t_build
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
-    prm = mka.solve_params(w.p, w.q, arith="fp64" if args.form == "fp64" else "mixed", cg_tol=1e-12,
+    cg_tol = 1e-12 if args.form == "fp64" else 1e-7
+    prm = mka.solve_params(w.p, w.q, arith="fp64" if args.form == "fp64" else "mixed", cg_tol=cg_tol,
                            keep_vectors=True)
     n_steps = args.warmup + args.steps
 

@@ -48,6 +48,8 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kMaxCl = MKA_MAX_CLUSTER_ATOMS;  // power of two (bitonic sort size bound)
 static_assert((kMaxCl & (kMaxCl - 1)) == 0, "cluster cap must be a power of two");
 
+__host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
 enum ColStatus { ST_OK = 0, ST_NOT_SPD = MKA_ERR_NOT_SPD, ST_NOCONV = MKA_ERR_NO_CONVERGENCE,
                  ST_BREAKDOWN = MKA_ERR_BREAKDOWN, ST_TOOLARGE = MKA_ERR_CLUSTER_TOO_LARGE };
 enum Src { SRC_E = 0, SRC_H = 1, SRC_S = 2 };
@@ -235,15 +237,19 @@ __device__ void sort_cluster(int* cl, int n) {
   }
 }
 
-// y = A x on the cluster (all four columns), rows 4t + i; x, y are [m][4].
+// y = A x on the cluster for the columns in `mask` (bit c = column c), rows 4t + i;
+// x, y are [m][4] in shared memory; other columns of y are left untouched.
 template <typename TV, typename T>
-__device__ __forceinline__ void spmm4(const TV* __restrict__ val, const int* lrow, const int* lcol,
-                                      const int* lblk, int ncl, const T* __restrict__ x, T* __restrict__ y) {
+__device__ __forceinline__ void spmm4(const TV* __restrict__ val, const int* lrow, const uint16_t* lcol,
+                                      const int* lblk, int ncl, const T* __restrict__ x, T* __restrict__ y,
+                                      int mask) {
   const int m = 4 * ncl;
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
     const int t = r >> 2, i = r & 3;
     T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-    for (int e = lrow[t]; e < lrow[t + 1]; ++e) {
+    const int e1 = lrow[t + 1];
+#pragma unroll 4
+    for (int e = lrow[t]; e < e1; ++e) {
       T v[4];
       RowLoad<TV, T>::load(val, lblk[e], i, v);
       const T* xb = x + (size_t)lcol[e] * 16;
@@ -255,203 +261,366 @@ __device__ __forceinline__ void spmm4(const TV* __restrict__ val, const int* lro
         a3 += v[k] * xb[4 * k + 3];
       }
     }
-    y[4 * r + 0] = a0;
-    y[4 * r + 1] = a1;
-    y[4 * r + 2] = a2;
-    y[4 * r + 3] = a3;
+    if (mask == 15) {
+      y[4 * r + 0] = a0;
+      y[4 * r + 1] = a1;
+      y[4 * r + 2] = a2;
+      y[4 * r + 3] = a3;
+    } else {
+      if (mask & 1) y[4 * r + 0] = a0;
+      if (mask & 2) y[4 * r + 1] = a1;
+      if (mask & 4) y[4 * r + 2] = a2;
+      if (mask & 8) y[4 * r + 3] = a3;
+    }
   }
   __syncthreads();
 }
 
-// Per-column dot products over the cluster rows, accumulated in double.
+// Per-column dot products over the cluster rows: per-thread partial sums in T
+// (a few terms each), combined across threads in FP64.
 template <typename T>
 __device__ __forceinline__ void dot4(const T* a, const T* b, int m, double* red, double* out) {
-  double acc[4] = {0, 0, 0, 0};
+  T part[4] = {0, 0, 0, 0};
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[c] += (double)a[4 * r + c] * (double)b[4 * r + c];
+    for (int c = 0; c < 4; ++c) part[c] += a[4 * r + c] * b[4 * r + c];
   }
+  double acc[4] = {(double)part[0], (double)part[1], (double)part[2], (double)part[3]};
   cta_sum4(acc, red, out);
 }
 
 // ---- shared state of one atom --------------------------------------------------------
 struct AtomState {
-  int n[4], src[4], seam_done[4], active[4], accept[4], act[4], next_s[4];
+  int n[4], src[4], seam_done[4], active[4], accept[4], act[4], next_s[4], proj[4];
   int it[4], cg_active[4], status[4];
   double beta_inv[4], csum[4], rr[4], alpha[4], beta_cg[4];
-  double tmp4[4];
-  int ncl, t0, flag, n_max;
+  int ncl, t0, flag, n_max, proj_any, acc_mask, act_mask;
 };
 
-// Parallel cyclic Jacobi on the symmetric nv x nv matrix A (leading dimension ld) in
-// shared memory; accumulates the rotations into Y (starts as I). Round-robin
-// ordering: ceil(nv/2) disjoint (p, q) pairs per round, nv' - 1 rounds per sweep.
-__device__ void jacobi_eig(double* A, double* Y, int nv, int ld, double* cs, double* red, int* flag) {
-  const int np = (nv + 1) / 2;           // pairs per round
-  const int n2 = 2 * np;                 // even number of players (one dummy when nv is odd)
-  for (int i = threadIdx.x; i < nv * nv; i += blockDim.x) Y[(i / nv) * ld + i % nv] = (i / nv == i % nv) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    // convergence: largest off-diagonal entry vs largest diagonal entry
-    double off = 0, dia = 0;
-    for (int i = threadIdx.x; i < nv * nv; i += blockDim.x) {
-      const int r = i / nv, c = i % nv;
-      const double v = fabs(A[r * ld + c]);
-      if (r == c) dia = fmax(dia, v); else off = fmax(off, v);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off = fmax(off, __shfl_xor_sync(0xffffffffu, off, o));
-      dia = fmax(dia, __shfl_xor_sync(0xffffffffu, dia, o));
-    }
-    if ((threadIdx.x & 31) == 0) {
-      red[(threadIdx.x >> 5) * 2] = off;
-      red[(threadIdx.x >> 5) * 2 + 1] = dia;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double o2 = 0, d2 = 0;
-      for (int k = 0; k < kWarps; ++k) {
-        o2 = fmax(o2, red[2 * k]);
-        d2 = fmax(d2, red[2 * k + 1]);
-      }
-      *flag = (o2 <= 1e-17 * d2) || o2 == 0.0;
-    }
-    __syncthreads();
-    if (*flag) break;
-    for (int round = 0; round < n2 - 1; ++round) {
-      // rotation angles of this round's pairs
-      for (int k = threadIdx.x; k < np; k += blockDim.x) {
-        int pp, qq;
-        if (k == 0) {
-          pp = 0;
-          qq = 1 + round;
-        } else {
-          pp = 1 + (round + k) % (n2 - 1);
-          qq = 1 + (round - k + n2 - 1) % (n2 - 1);
-        }
-        if (pp > qq) { const int t = pp; pp = qq; qq = t; }
-        double c = 1.0, s = 0.0;
-        if (qq < nv) {
-          const double apq = A[pp * ld + qq];
-          if (apq != 0.0) {
-            const double app = A[pp * ld + pp], aqq = A[qq * ld + qq];
-            const double theta = (aqq - app) / (2.0 * apq);
-            const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
-            s = t * c;
-          }
-        }
-        cs[4 * k + 0] = c;
-        cs[4 * k + 1] = s;
-        reinterpret_cast<int*>(cs)[8 * k + 4] = pp;   // indices packed behind (c, s)
-        reinterpret_cast<int*>(cs)[8 * k + 5] = qq;
-      }
-      __syncthreads();
-      // A <- A J (columns p, q) and Y <- Y J
-      for (int idx = threadIdx.x; idx < np * nv; idx += blockDim.x) {
-        const int k = idx / nv, r = idx % nv;
-        const int pp = reinterpret_cast<int*>(cs)[8 * k + 4], qq = reinterpret_cast<int*>(cs)[8 * k + 5];
-        if (qq >= nv) continue;
-        const double c = cs[4 * k], s = cs[4 * k + 1];
-        const double ap = A[r * ld + pp], aq = A[r * ld + qq];
-        A[r * ld + pp] = c * ap - s * aq;
-        A[r * ld + qq] = s * ap + c * aq;
-        const double yp = Y[r * ld + pp], yq = Y[r * ld + qq];
-        Y[r * ld + pp] = c * yp - s * yq;
-        Y[r * ld + qq] = s * yp + c * yq;
-      }
-      __syncthreads();
-      // A <- J^T A (rows p, q)
-      for (int idx = threadIdx.x; idx < np * nv; idx += blockDim.x) {
-        const int k = idx / nv, r = idx % nv;
-        const int pp = reinterpret_cast<int*>(cs)[8 * k + 4], qq = reinterpret_cast<int*>(cs)[8 * k + 5];
-        if (qq >= nv) continue;
-        const double c = cs[4 * k], s = cs[4 * k + 1];
-        const double ap = A[pp * ld + r], aq = A[qq * ld + r];
-        A[pp * ld + r] = c * ap - s * aq;
-        A[qq * ld + r] = s * ap + c * aq;
-      }
-      __syncthreads();
-    }
-  }
+// ---- warp-level FP64 reduced solve ------------------------------------------------------
+// Every function here is run by one whole warp on nv x nv matrices in shared memory
+// (row-major, leading dimension ld); lanes own rows or columns.
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
-// Reduced problem of one column: Hr, Sr in shared memory (nv x nv, leading dimension ld).
-// On return eps_sorted[0..nv) ascending and C (ld) = L^{-T} Y with columns in that order.
-// Returns false when S_r is not positive definite.
-__device__ bool reduced_solve(double* Hr, double* Sr, double* Y, double* C, double* eps, int nv, int ld,
-                              double* cs, double* red, int* flag) {
-  // Cholesky S_r = L L^T in place (lower triangle of Sr), right-looking.
-  for (int k = 0; k < nv; ++k) {
-    if (threadIdx.x == 0) {
-      const double d = Sr[k * ld + k];
-      *flag = d > 0.0;
-      Sr[k * ld + k] = d > 0.0 ? sqrt(d) : 1.0;
+// S = L L^T in place (lower triangle), rdiag[i] = 1 / L_ii. False when S is not positive definite.
+__device__ bool warp_cholesky(double* S, int n, int ld, double* rdiag) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k < n; ++k) {
+    const double d = S[k * ld + k];
+    __syncwarp();
+    if (!(d > 0.0)) return false;
+    const double lkk = sqrt(d), inv = 1.0 / lkk;
+    if (lane == 0) {
+      S[k * ld + k] = lkk;
+      rdiag[k] = inv;
     }
-    __syncthreads();
-    if (!*flag) return false;
-    const double lkk = Sr[k * ld + k];
-    for (int i = k + 1 + threadIdx.x; i < nv; i += blockDim.x) Sr[i * ld + k] /= lkk;
-    __syncthreads();
-    const int rem = nv - k - 1;
-    for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
-      const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
-      if (j <= i) Sr[i * ld + j] -= Sr[i * ld + k] * Sr[j * ld + k];
+    for (int i = k + 1 + lane; i < n; i += 32) S[i * ld + k] *= inv;
+    __syncwarp();
+    for (int i = k + 1 + lane; i < n; i += 32) {
+      const double lik = S[i * ld + k];
+      for (int j = k + 1; j <= i; ++j) S[i * ld + j] -= lik * S[j * ld + k];
     }
-    __syncthreads();
+    __syncwarp();
   }
-  // X = L^{-1} Hr (column by column, forward substitution) into C
-  for (int n = threadIdx.x; n < nv; n += blockDim.x) {
-    for (int i = 0; i < nv; ++i) {
-      double v = Hr[i * ld + n];
-      for (int k = 0; k < i; ++k) v -= Sr[i * ld + k] * C[k * ld + n];
-      C[i * ld + n] = v / Sr[i * ld + i];
-    }
-  }
-  __syncthreads();
-  // A = L^{-1} X^T into Hr (A = L^{-1} Hr L^{-T})
-  for (int n = threadIdx.x; n < nv; n += blockDim.x) {
-    for (int i = 0; i < nv; ++i) {
-      double v = C[n * ld + i];
-      for (int k = 0; k < i; ++k) v -= Sr[i * ld + k] * Hr[k * ld + n];
-      Hr[i * ld + n] = v / Sr[i * ld + i];
-    }
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < nv * nv; idx += blockDim.x) {
-    const int i = idx / nv, j = idx % nv;
-    if (j > i) {
-      const double v = 0.5 * (Hr[i * ld + j] + Hr[j * ld + i]);
-      Hr[i * ld + j] = v;
-      Hr[j * ld + i] = v;
-    }
-  }
-  __syncthreads();
-  jacobi_eig(Hr, Y, nv, ld, cs, red, flag);
-  // ranks of the eigenvalues (ascending, ties by index)
-  int* rank = reinterpret_cast<int*>(red);
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-    const double e = Hr[i * ld + i];
-    int r = 0;
-    for (int k = 0; k < nv; ++k) {
-      const double f = Hr[k * ld + k];
-      r += (f < e) || (f == e && k < i);
-    }
-    rank[i] = r;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) eps[rank[i]] = Hr[i * ld + i];
-  // C = L^{-T} Y, column alpha stored at its rank
-  for (int a = threadIdx.x; a < nv; a += blockDim.x) {
-    const int ra = rank[a];
-    for (int i = nv - 1; i >= 0; --i) {
-      double v = Y[i * ld + a];
-      for (int k = i + 1; k < nv; ++k) v -= Sr[k * ld + i] * C[k * ld + ra];
-      C[i * ld + ra] = v / Sr[i * ld + i];
-    }
-  }
-  __syncthreads();
   return true;
+}
+
+// H <- L^{-1} H L^{-T} for symmetric H (full storage), then symmetrised.
+__device__ void warp_congruence(double* H, const double* L, const double* rdiag, int n, int ld) {
+  const int lane = threadIdx.x & 31;
+  for (int j = lane; j < n; j += 32)          // X = L^{-1} H, column j by forward substitution
+    for (int i = 0; i < n; ++i) {
+      double v = H[i * ld + j];
+      for (int k = 0; k < i; ++k) v -= L[i * ld + k] * H[k * ld + j];
+      H[i * ld + j] = v * rdiag[i];
+    }
+  __syncwarp();
+  for (int i = lane; i < n; i += 32)          // A = X L^{-T}, row i by forward substitution
+    for (int j = 0; j < n; ++j) {
+      double v = H[i * ld + j];
+      for (int k = 0; k < j; ++k) v -= H[i * ld + k] * L[j * ld + k];
+      H[i * ld + j] = v * rdiag[j];
+    }
+  __syncwarp();
+  for (int i = lane; i < n; i += 32)
+    for (int j = 0; j < i; ++j) {
+      const double v = 0.5 * (H[i * ld + j] + H[j * ld + i]);
+      H[i * ld + j] = v;
+      H[j * ld + i] = v;
+    }
+  __syncwarp();
+}
+
+// Householder reduction of the symmetric A to tridiagonal form T = Q^T A Q: diagonal d,
+// off-diagonal e (e[k] couples k and k+1, e[n-1] = 0). On return A holds Q (accumulated in
+// place from the Householder vectors kept below the subdiagonal). p, tau: n doubles each.
+__device__ void warp_tridiag(double* A, int n, int ld, double* d, double* e, double* p, double* tau) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k + 2 < n; ++k) {
+    double s2 = 0.0;
+    for (int i = k + 1 + lane; i < n; i += 32) s2 += A[i * ld + k] * A[i * ld + k];
+    s2 = warp_sum_d(s2);
+    const double x0 = A[(k + 1) * ld + k];
+    const double nrm = sqrt(s2);
+    const double alpha = x0 >= 0.0 ? -nrm : nrm;
+    const double v0 = x0 - alpha;
+    const double vtv = s2 - x0 * x0 + v0 * v0;
+    const double tk = vtv > 0.0 ? 2.0 / vtv : 0.0;          // H_k = I - tk v v^T
+    __syncwarp();
+    if (lane == 0) {
+      A[(k + 1) * ld + k] = v0;                              // v = A[k+1.., k]
+      d[k] = A[k * ld + k];
+      e[k] = alpha;
+      tau[k] = tk;
+    }
+    __syncwarp();
+    for (int i = k + 1 + lane; i < n; i += 32) {             // p = tk B v
+      double acc = 0.0;
+      for (int j = k + 1; j < n; ++j) acc += A[i * ld + j] * A[j * ld + k];
+      p[i] = tk * acc;
+    }
+    __syncwarp();
+    double pv = 0.0;
+    for (int i = k + 1 + lane; i < n; i += 32) pv += p[i] * A[i * ld + k];
+    pv = warp_sum_d(pv);
+    const double kc = 0.5 * tk * pv;
+    __syncwarp();
+    for (int i = k + 1 + lane; i < n; i += 32) p[i] -= kc * A[i * ld + k];   // w = p - kc v
+    __syncwarp();
+    for (int i = k + 1 + lane; i < n; i += 32) {             // B -= v w^T + w v^T
+      const double vi = A[i * ld + k], wi = p[i];
+      for (int j = k + 1; j < n; ++j) A[i * ld + j] -= vi * p[j] + wi * A[j * ld + k];
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (n >= 2) {
+      d[n - 2] = A[(n - 2) * ld + (n - 2)];
+      e[n - 2] = A[(n - 1) * ld + (n - 2)];
+    }
+    d[n - 1] = A[(n - 1) * ld + (n - 1)];
+    e[n - 1] = 0.0;
+  }
+  __syncwarp();
+  // Q = H_0 H_1 ... H_{n-3}, accumulated backwards in place: before H_k is applied the
+  // trailing block [k+1.., k+1..] holds H_{k+1}...H_{n-3}; v_k sits in column k.
+  const int k0 = n >= 2 ? n - 2 : 0;
+  for (int i = k0 + lane; i < n; i += 32)
+    for (int j = k0; j < n; ++j) A[i * ld + j] = (i == j) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int k = n - 3; k >= 0; --k) {
+    const int b = k + 1;
+    // grow the block by row/column b (identity there), keeping v_k in column k
+    for (int j = b + lane; j < n; j += 32) {
+      A[b * ld + j] = (j == b) ? 1.0 : 0.0;
+      A[j * ld + b] = (j == b) ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    const double tk = tau[k];
+    if (tk != 0.0) {
+      for (int j = b + lane; j < n; j += 32) {               // p_j = tk sum_i v_i Q_ij
+        double y = 0.0;
+        for (int i = b; i < n; ++i) y += A[i * ld + k] * A[i * ld + j];
+        p[j] = tk * y;
+      }
+      __syncwarp();
+      for (int i = b + lane; i < n; i += 32) {
+        const double vi = A[i * ld + k];
+        for (int j = b; j < n; ++j) A[i * ld + j] -= vi * p[j];
+      }
+      __syncwarp();
+    }
+  }
+  for (int j = lane; j < n; j += 32) {                       // row / column 0 of Q
+    A[j] = (j == 0) ? 1.0 : 0.0;
+    A[j * ld] = (j == 0) ? 1.0 : 0.0;
+  }
+  __syncwarp();
+}
+
+// Eigenvalues of the symmetric tridiagonal (d, e) by the implicit-shift QL method
+// (Bowdler, Martin, Reinsch & Wilkinson, Numer. Math. 11, 1968), with every rotation also
+// applied to the columns of Z. Lane 0 runs the scalar recurrence of one sweep and records
+// its rotations (rc, rs); then every lane applies them to its rows of Z in order.
+// Returns false when an eigenvalue needs more than 60 sweeps.
+__device__ bool warp_tql(double* d, double* e, double* Z, int n, int ld, double* rc, double* rs, int* ctl) {
+  const int lane = threadIdx.x & 31;
+  for (int l = 0; l < n; ++l) {
+    for (int iter = 0;; ++iter) {
+      // ctl[0] = m (end of the unreduced block), ctl[1] = first recorded rotation index, ctl[2] = status
+      if (lane == 0) {
+        int m = l;
+        for (; m < n - 1; ++m) {
+          const double dd = fabs(d[m]) + fabs(d[m + 1]);
+          if (fabs(e[m]) <= 2.2204460492503131e-16 * dd) break;
+        }
+        ctl[0] = m;
+        ctl[1] = m;          // no rotation recorded yet
+        ctl[2] = 0;
+        if (m != l) {
+          if (iter == 60) {
+            ctl[2] = 1;
+          } else {
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = sqrt(g * g + 1.0);
+            g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
+            double s = 1.0, c = 1.0, p = 0.0;
+            bool early = false;
+            int i = m - 1;
+            for (; i >= l; --i) {
+              const double f = s * e[i], b = c * e[i];
+              r = sqrt(f * f + g * g);
+              e[i + 1] = r;
+              if (r == 0.0) {
+                d[i + 1] -= p;
+                e[m] = 0.0;
+                early = true;
+                break;
+              }
+              const double rinv = 1.0 / r;
+              s = f * rinv;
+              c = g * rinv;
+              g = d[i + 1] - p;
+              r = (d[i] - g) * s + 2.0 * c * b;
+              p = s * r;
+              d[i + 1] = g + p;
+              g = c * r - b;
+              rc[i] = c;
+              rs[i] = s;
+            }
+            ctl[1] = early ? i + 1 : l;
+            if (!early) {
+              d[l] -= p;
+              e[l] = g;
+              e[m] = 0.0;
+            }
+          }
+        }
+      }
+      __syncwarp();
+      const int m = ctl[0], i0 = ctl[1];
+      if (ctl[2]) return false;
+      if (m == l) break;
+      if (Z) {
+        for (int k = lane; k < n; k += 32) {
+          for (int i = m - 1; i >= i0; --i) {
+            const double c = rc[i], s = rs[i];
+            const double f = Z[k * ld + i + 1];
+            Z[k * ld + i + 1] = s * Z[k * ld + i] + c * f;
+            Z[k * ld + i] = c * Z[k * ld + i] - s * f;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+  return true;
+}
+
+// Per-warp scratch of the reduced solve (doubles): rdiag, e, p, tau, rc, rs (n each),
+// 4 control ints, the ranks (n ints) and the eigenvalues (n).
+__host__ __device__ constexpr size_t red_scratch_doubles(int nu) { return (size_t)6 * nu + 2 + (nu + 1) / 2 + nu; }
+
+struct RedScratch {
+  double *rdiag, *e, *p, *tau, *rc, *rs, *evals;
+  int *ctl, *rank;
+  __device__ RedScratch(double* w, int nu) {
+    rdiag = w;
+    e = w + nu;
+    p = w + 2 * nu;
+    tau = w + 3 * nu;
+    rc = w + 4 * nu;
+    rs = w + 5 * nu;
+    ctl = reinterpret_cast<int*>(w + 6 * nu);
+    rank = reinterpret_cast<int*>(w + 6 * nu + 2);
+    evals = w + 6 * nu + 2 + (nu + 1) / 2;
+  }
+};
+
+// Reduced problem of one column (Eq. EQ-SUB-EIG-VEC with S_r formed explicitly): Cholesky of S_r
+// (in Lm), A = L^{-1} H_r L^{-T}, tridiagonalisation, QL; on return Hm holds C = L^{-T} Q Z
+// (column a = eigenvector a, unsorted), evals[a] its eigenvalue and rank[a] its ascending
+// position. False when S_r is not positive definite or QL fails.
+__device__ bool warp_reduced_solve(double* Hm, double* Lm, int n, int ld, const RedScratch& w) {
+  const int lane = threadIdx.x & 31;
+  if (!warp_cholesky(Lm, n, ld, w.rdiag)) return false;
+  warp_congruence(Hm, Lm, w.rdiag, n, ld);
+  warp_tridiag(Hm, n, ld, w.evals, w.e, w.p, w.tau);
+  if (!warp_tql(w.evals, w.e, Hm, n, ld, w.rc, w.rs, w.ctl)) return false;
+  for (int a = lane; a < n; a += 32)            // C = L^{-T} Z, column a by back substitution, in place
+    for (int i = n - 1; i >= 0; --i) {
+      double v = Hm[i * ld + a];
+      for (int k = i + 1; k < n; ++k) v -= Lm[k * ld + i] * Hm[k * ld + a];
+      Hm[i * ld + a] = v * w.rdiag[i];
+    }
+  for (int a = lane; a < n; a += 32) {
+    const double ea = w.evals[a];
+    int r = 0;
+    for (int k = 0; k < n; ++k) {
+      const double f = w.evals[k];
+      r += (f < ea) || (f == ea && k < a);
+    }
+    w.rank[a] = r;
+  }
+  __syncwarp();
+  return true;
+}
+
+// One Gram-Schmidt coefficient sweep over u_0..u_{nmax-1} (one warp per vector, lanes over
+// rows): coef[mm][c] = (S u_mm)^T l for columns whose basis holds mm (when do_coef), and, for
+// columns with a pending projection column pn = n - 1, H_r[mm][pn] = u_mm^T (H u_pn) and
+// S_r[mm][pn] = u_mm^T (S u_pn) written (with their mirror) to HS.
+template <typename T>
+__device__ void gs_sweep(const T* U, const T* SU, const T* L, const T* KV, const T* SV, int m, int m_cap, int nmax,
+                         bool do_coef, const AtomState& st, double* coef, double* HS, int nu) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const bool proj = st.proj_any;
+  for (int mm = wid; mm < nmax; mm += kWarps) {
+    const T* su = SU + (size_t)mm * m_cap * 4;
+    const T* u = U + (size_t)mm * m_cap * 4;
+    T pc[4] = {0, 0, 0, 0}, ph[4] = {0, 0, 0, 0}, ps[4] = {0, 0, 0, 0};
+    for (int r = lane; r < m; r += 32) {
+      if (do_coef) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) pc[c] += su[4 * r + c] * L[4 * r + c];
+      }
+      if (proj) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const T uv = u[4 * r + c];
+          ph[c] += uv * KV[4 * r + c];
+          ps[c] += uv * SV[4 * r + c];
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (do_coef) pc[c] = warp_sum(pc[c]);
+      if (proj) {
+        ph[c] = warp_sum(ph[c]);
+        ps[c] = warp_sum(ps[c]);
+      }
+    }
+    if (lane < 4) {
+      const int c = lane;
+      if (do_coef) coef[mm * 4 + c] = (st.active[c] && mm < st.n[c]) ? (double)pc[c] : 0.0;
+      if (proj && st.proj[c] && mm < st.n[c]) {
+        const int pn = st.n[c] - 1;
+        double* H = HS + (size_t)c * 2 * nu * nu;
+        double* S = H + (size_t)nu * nu;
+        H[mm * nu + pn] = (double)ph[c];
+        H[pn * nu + mm] = (double)ph[c];
+        S[mm * nu + pn] = (double)ps[c];
+        S[pn * nu + mm] = (double)ps[c];
+      }
+    }
+  }
+  __syncthreads();
 }
 
 template <typename TV, typename T>
@@ -466,31 +635,25 @@ __global__ void __launch_bounds__(kThreads) atoms_kernel(const Args<TV> A) {
 
   const int nu = A.nu;
   const int ld = nu + 1;
-  int* cl = reinterpret_cast<int*>(smem_raw);                 // kMaxCl
-  int* lrow = cl + kMaxCl;                                     // kMaxCl + 1
-  int* lcol = lrow + kMaxCl + 1;                               // lnnz_cap
-  int* lblk = lcol + A.lnnz_cap;                               // lnnz_cap
-  size_t off = (size_t)(2 * kMaxCl + 1 + 2 * A.lnnz_cap) * sizeof(int);
-  off = (off + 15) & ~(size_t)15;
-  double* Hr = reinterpret_cast<double*>(smem_raw + off);     // nu x ld
-  double* Sr = Hr + nu * ld;
-  double* Y = Sr + nu * ld;
-  double* C = Y + nu * ld;
-  double* evals = C + nu * ld;                                 // nu
-  double* cs = evals + nu;                                     // 4 x ceil(nu/2) (+ packed ints)
-
   const int m_cap = A.mcap;
-  T* base = reinterpret_cast<T*>(A.scratch + (size_t)blockIdx.x * A.slot_bytes);
-  T* U = base;                                   // [nu][m][4]
-  T* SU = U + (size_t)nu * m_cap * 4;
-  T* Kv = SU + (size_t)nu * m_cap * 4;
-  T* l = Kv + (size_t)nu * m_cap * 4;            // [m][4]
-  T* Sl = l + (size_t)m_cap * 4;
-  T* kv = Sl + (size_t)m_cap * 4;
-  T* sv = kv + (size_t)m_cap * 4;                // s_j (CG solution)
-  T* rv = sv + (size_t)m_cap * 4;
-  T* pv = rv + (size_t)m_cap * 4;
-  T* Ap = pv + (size_t)m_cap * 4;
+  int* cl = reinterpret_cast<int*>(smem_raw);                            // kMaxCl
+  int* lrow = cl + kMaxCl;                                                // kMaxCl + 1
+  int* lblk = lrow + kMaxCl + 1;                                          // lnnz_cap
+  uint16_t* lcol = reinterpret_cast<uint16_t*>(lblk + A.lnnz_cap);        // lnnz_cap
+  size_t off = (size_t)(2 * kMaxCl + 1 + A.lnnz_cap) * sizeof(int) + (size_t)A.lnnz_cap * sizeof(uint16_t);
+  off = (off + 15) & ~(size_t)15;
+  unsigned char* region = smem_raw + off;   // work vectors during CG and basis; reduced matrices afterwards
+  T* V0 = reinterpret_cast<T*>(region);     // CG: p     basis: l
+  T* V1 = V0 + (size_t)m_cap * 4;           // CG: S p   basis: S l, then S u_{n-1}
+  T* V2 = V1 + (size_t)m_cap * 4;           // CG: r     basis: H u_{n-1}
+  double* RM = reinterpret_cast<double*>(region);   // per column: H_r / C (nu x ld), S_r / L, 8 nu scratch
+  const size_t rm_col = (size_t)2 * nu * ld + red_scratch_doubles(nu);
+
+  char* slot = A.scratch + (size_t)blockIdx.x * A.slot_bytes;
+  T* U = reinterpret_cast<T*>(slot);                 // [nu][m_cap][4]
+  T* SU = U + (size_t)nu * m_cap * 4;                // [nu][m_cap][4]
+  T* SJ = SU + (size_t)nu * m_cap * 4;               // s_j, [m_cap][4]
+  double* HS = reinterpret_cast<double*>(slot + align_up(sizeof(T) * ((size_t)2 * nu + 1) * m_cap * 4, 256));
 
   for (;;) {
     if (threadIdx.x == 0) {
@@ -520,7 +683,6 @@ __global__ void __launch_bounds__(kThreads) atoms_kernel(const Args<TV> A) {
     }
     const int ncl = ncl_raw;
     sort_cluster(cl, ncl);
-    // local pattern: count, prefix, fill
     for (int t = threadIdx.x; t < ncl; t += blockDim.x) {
       const int b = cl[t];
       int c = 0;
@@ -547,7 +709,7 @@ __global__ void __launch_bounds__(kThreads) atoms_kernel(const Args<TV> A) {
       for (int k = A.row_ptr[b]; k < A.row_ptr[b + 1]; ++k) {
         const int lc = find_local(cl, ncl, A.col[k]);
         if (lc >= 0) {
-          lcol[e] = lc;
+          lcol[e] = (uint16_t)lc;
           lblk[e] = k;
           ++e;
         }
@@ -556,12 +718,15 @@ __global__ void __launch_bounds__(kThreads) atoms_kernel(const Args<TV> A) {
     const int m = 4 * ncl;
     const int t0 = st.t0;
     // ---- 2. inner CG: S s = e_j, x0 = 0 ----------------------------------------------
+    T* P = V0;
+    T* AP = V1;
+    T* R = V2;
     for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
       const int r = i >> 2, c = i & 3;
       const T e = (r == 4 * t0 + c) ? (T)1 : (T)0;
-      sv[i] = 0;
-      rv[i] = e;
-      pv[i] = e;
+      SJ[i] = 0;
+      R[i] = e;
+      P[i] = e;
     }
     if (threadIdx.x < 4) {
       const int c = threadIdx.x;
@@ -572,9 +737,10 @@ __global__ void __launch_bounds__(kThreads) atoms_kernel(const Args<TV> A) {
     }
     __syncthreads();
     for (int it = 0; it < A.cg_maxit; ++it) {
-      if (!(st.cg_active[0] | st.cg_active[1] | st.cg_active[2] | st.cg_active[3])) break;
-      spmm4<TV, T>(A.valS, lrow, lcol, lblk, ncl, pv, Ap);
-      dot4<T>(pv, Ap, m, red, sums);
+      const int cmask = st.cg_active[0] | (st.cg_active[1] << 1) | (st.cg_active[2] << 2) | (st.cg_active[3] << 3);
+      if (!cmask) break;
+      spmm4<TV, T>(A.valS, lrow, lcol, lblk, ncl, P, AP, cmask);
+      dot4<T>(P, AP, m, red, sums);
       if (threadIdx.x < 4) {
         const int c = threadIdx.x;
         double a = 0.0;
@@ -593,12 +759,12 @@ __global__ void __launch_bounds__(kThreads) atoms_kernel(const Args<TV> A) {
         const int c = i & 3;
         if (st.cg_active[c]) {
           const T a = (T)st.alpha[c];
-          sv[i] += a * pv[i];
-          rv[i] -= a * Ap[i];
+          SJ[i] += a * P[i];
+          R[i] -= a * AP[i];
         }
       }
       __syncthreads();
-      dot4<T>(rv, rv, m, red, sums);
+      dot4<T>(R, R, m, red, sums);
       if (threadIdx.x < 4) {
         const int c = threadIdx.x;
         if (st.cg_active[c]) {
@@ -611,71 +777,61 @@ __global__ void __launch_bounds__(kThreads) atoms_kernel(const Args<TV> A) {
       __syncthreads();
       for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
         const int c = i & 3;
-        if (st.cg_active[c]) pv[i] = rv[i] + (T)st.beta_cg[c] * pv[i];
+        if (st.cg_active[c]) P[i] = R[i] + (T)st.beta_cg[c] * P[i];
       }
       __syncthreads();
     }
+    // ---- 3. multiple Arnoldi basis, with the projection accumulated on the way ---------
+    T* Lv = V0;
+    T* SL = V1;
+    T* KV = V2;
     if (threadIdx.x < 4) {
       const int c = threadIdx.x;
       if (st.cg_active[c] && st.status[c] == ST_OK) st.status[c] = ST_NOCONV;
-      // ---- 3. basis state ----
       st.n[c] = 0;
       st.src[c] = SRC_E;
       st.seam_done[c] = (A.q == 0);
       st.active[c] = (st.status[c] == ST_OK);
+      st.proj[c] = 0;
     }
+    if (threadIdx.x == 0) st.proj_any = 0;
     for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
       const int r = i >> 2, c = i & 3;
-      l[i] = (r == 4 * t0 + c) ? (T)1 : (T)0;
+      Lv[i] = (r == 4 * t0 + c) ? (T)1 : (T)0;
     }
     __syncthreads();
-
-    // ---- 3. multiple Arnoldi basis ---------------------------------------------------------
     for (int guard = 0; guard < nu + 4; ++guard) {
       if (!(st.active[0] | st.active[1] | st.active[2] | st.active[3])) break;
       if (threadIdx.x == 0) {
         int nm = 0;
         for (int c = 0; c < 4; ++c) {
           st.csum[c] = 0.0;
-          if (st.active[c]) nm = max(nm, st.n[c]);
+          if (st.active[c] || st.proj[c]) nm = max(nm, st.n[c]);
         }
         st.n_max = nm;
       }
       __syncthreads();
       const int nmax = st.n_max;
       for (int pass = 0; pass < 2 && nmax > 0; ++pass) {
-        // coefficients (S u_mm)^T l, one warp per mm
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        for (int mm = wid; mm < nmax; mm += kWarps) {
-          const T* su = SU + (size_t)mm * m_cap * 4;
-          double acc[4] = {0, 0, 0, 0};
-          for (int r = lane; r < m; r += 32) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[c] += (double)su[4 * r + c] * (double)l[4 * r + c];
-          }
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[c] = warp_sum(acc[c]);
-          if (lane < 4) {
-            const int c = lane;
-            coef[mm * 4 + c] = (st.active[c] && mm < st.n[c]) ? acc[c] : 0.0;
-          }
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
-          const int r = i >> 2, c = i & 3;
-          T v = l[i];
-          for (int mm = 0; mm < nmax; ++mm) v -= (T)coef[mm * 4 + c] * U[(size_t)mm * m_cap * 4 + 4 * r + c];
-          l[i] = v;
-        }
+        gs_sweep<T>(U, SU, Lv, KV, SL, m, m_cap, nmax, true, st, coef, HS, nu);
         if (threadIdx.x < 4) {
           double s = 0;
           for (int mm = 0; mm < nmax; ++mm) s += coef[mm * 4 + threadIdx.x] * coef[mm * 4 + threadIdx.x];
           st.csum[threadIdx.x] += s;
+          st.proj[threadIdx.x] = 0;
+        }
+        if (threadIdx.x == 0) st.proj_any = 0;
+        for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
+          const int r = i >> 2, c = i & 3;
+          T v = Lv[i];
+          for (int mm = 0; mm < nmax; ++mm) v -= (T)coef[mm * 4 + c] * U[(size_t)mm * m_cap * 4 + 4 * r + c];
+          Lv[i] = v;
         }
         __syncthreads();
       }
-      spmm4<TV, T>(A.valS, lrow, lcol, lblk, ncl, l, Sl);
-      dot4<T>(l, Sl, m, red, sums);
+      const int amask = st.active[0] | (st.active[1] << 1) | (st.active[2] << 2) | (st.active[3] << 3);
+      spmm4<TV, T>(A.valS, lrow, lcol, lblk, ncl, Lv, SL, amask);
+      dot4<T>(Lv, SL, m, red, sums);
       if (threadIdx.x < 4) {
         const int c = threadIdx.x;
         st.accept[c] = 0;
@@ -700,32 +856,30 @@ __global__ void __launch_bounds__(kThreads) atoms_kernel(const Args<TV> A) {
         }
       }
       __syncthreads();
-      const bool any_acc = st.accept[0] | st.accept[1] | st.accept[2] | st.accept[3];
-      if (any_acc) {
+      const int acc_mask = st.accept[0] | (st.accept[1] << 1) | (st.accept[2] << 2) | (st.accept[3] << 3);
+      if (acc_mask) {
         for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
           const int r = i >> 2, c = i & 3;
           if (st.accept[c]) {
             const T bi = (T)st.beta_inv[c];
-            const T u = l[i] * bi;
+            const T u = Lv[i] * bi;
+            const T su = SL[i] * bi;
             const size_t o = (size_t)st.n[c] * m_cap * 4 + 4 * r + c;
             U[o] = u;
-            SU[o] = Sl[i] * bi;
-            l[i] = u;
+            SU[o] = su;
+            Lv[i] = u;
+            SL[i] = su;               // S u_n, kept for the projection column
           }
         }
         __syncthreads();
-        spmm4<TV, T>(A.valH, lrow, lcol, lblk, ncl, l, kv);
-        for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
-          const int r = i >> 2, c = i & 3;
-          if (st.accept[c]) Kv[(size_t)st.n[c] * m_cap * 4 + 4 * r + c] = kv[i];
-        }
-        __syncthreads();
+        spmm4<TV, T>(A.valH, lrow, lcol, lblk, ncl, Lv, KV, acc_mask);   // H u_n, accepted columns only
       }
       if (threadIdx.x < 4) {
         const int c = threadIdx.x;
         st.next_s[c] = 0;
         if (st.accept[c]) {
           st.n[c] += 1;
+          st.proj[c] = 1;
           if (st.n[c] >= nu) {
             st.active[c] = 0;
           } else if (st.n[c] == A.p && !st.seam_done[c]) {
@@ -737,117 +891,127 @@ __global__ void __launch_bounds__(kThreads) atoms_kernel(const Args<TV> A) {
           }
         }
       }
+      if (threadIdx.x == 0) st.proj_any = acc_mask != 0;
       __syncthreads();
       for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
-        const int r = i >> 2, c = i & 3;
+        const int c = i & 3;
         if (!st.active[c]) continue;
         if (st.accept[c]) {
-          l[i] = st.next_s[c] ? sv[i] : kv[i];
+          Lv[i] = st.next_s[c] ? SJ[i] : KV[i];
         } else if (st.act[c] == ACT_LOAD_K) {
-          l[i] = Kv[(size_t)(st.n[c] - 1) * m_cap * 4 + 4 * r + c];
+          Lv[i] = KV[i];
         } else if (st.act[c] == ACT_LOAD_S) {
-          l[i] = sv[i];
+          Lv[i] = SJ[i];
         }
       }
       __syncthreads();
     }
+    // projection columns still pending (the last accepted vector of each column)
+    if (st.proj_any) {
+      if (threadIdx.x == 0) {
+        int nm = 0;
+        for (int c = 0; c < 4; ++c)
+          if (st.proj[c]) nm = max(nm, st.n[c]);
+        st.n_max = nm;
+      }
+      __syncthreads();
+      gs_sweep<T>(U, SU, Lv, KV, SL, m, m_cap, st.n_max, false, st, coef, HS, nu);
+    }
 
-    // ---- 4./5. projection, reduced solve, outputs, one column at a time ----------------
+    // ---- 4./5. reduced problems (one warp per column) and outputs ----------------------
+    // H_r, S_r into shared memory (the work vectors are no longer needed)
     for (int c = 0; c < 4; ++c) {
+      const int nv = st.n[c];
+      double* Hm = RM + (size_t)c * rm_col;
+      double* Lm = Hm + (size_t)nu * ld;
+      const double* H = HS + (size_t)c * 2 * nu * nu;
+      const double* S = H + (size_t)nu * nu;
+      for (int i = threadIdx.x; i < nv * nv; i += blockDim.x) {
+        const int a = i / nv, b = i % nv;
+        Hm[a * ld + b] = H[a * nu + b];
+        Lm[a * ld + b] = S[a * nu + b];
+      }
+    }
+    __syncthreads();
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (wid < 4) {
+      const int c = wid;
       const int64_t col = 4 * widx + c;
       const int nv = st.n[c];
+      double* Hm = RM + (size_t)c * rm_col;
+      double* Lm = Hm + (size_t)nu * ld;
+      const RedScratch wsc(Lm + (size_t)nu * ld, nu);
       int stc = st.status[c];
       if (stc == ST_OK && nv < nu) stc = ST_BREAKDOWN;
       bool ok = (st.status[c] == ST_OK) && nv > 0;
-      if (ok) {
-        // Hr = U^T K, Sr = U^T SU, then symmetrised
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        for (int e = wid; e < nv * nv; e += kWarps) {
-          const int a = e / nv, b = e % nv;
-          const T* ua = U + (size_t)a * m_cap * 4;
-          const T* kb = Kv + (size_t)b * m_cap * 4;
-          const T* sb = SU + (size_t)b * m_cap * 4;
-          double h = 0, s = 0;
-          for (int r = lane; r < m; r += 32) {
-            const double u = (double)ua[4 * r + c];
-            h += u * (double)kb[4 * r + c];
-            s += u * (double)sb[4 * r + c];
-          }
-          h = warp_sum(h);
-          s = warp_sum(s);
-          if (lane == 0) {
-            Hr[a * ld + b] = h;
-            Sr[a * ld + b] = s;
-          }
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < nv * nv; e += blockDim.x) {
-          const int a = e / nv, b = e % nv;
-          if (b > a) {
-            const double h = 0.5 * (Hr[a * ld + b] + Hr[b * ld + a]);
-            const double s = 0.5 * (Sr[a * ld + b] + Sr[b * ld + a]);
-            Hr[a * ld + b] = h;
-            Hr[b * ld + a] = h;
-            Sr[a * ld + b] = s;
-            Sr[b * ld + a] = s;
-          }
-        }
-        __syncthreads();
-        ok = reduced_solve(Hr, Sr, Y, C, evals, nv, ld, cs, red, &st.flag);
-        if (!ok) stc = ST_NOT_SPD;
-      }
-      if (threadIdx.x == 0) {
+      if (ok) ok = warp_reduced_solve(Hm, Lm, nv, ld, wsc);
+      if (!ok && st.status[c] == ST_OK) stc = ST_NOT_SPD;
+      if (lane == 0) {
         A.status[col] = stc;
         A.nu_eff[col] = ok ? nv : 0;
         A.cg_iters[col] = st.it[c];
+        st.accept[c] = ok;    // reused as "reduced solve succeeded"
       }
-      // eps, w = V_j (S V)_j with V = U C
-      const int jr = 4 * t0 + c;
-      for (int a = threadIdx.x; a < nu; a += blockDim.x) {
-        double e = 0.0, wv = 0.0;
-        if (ok && a < nv) {
-          double vj = 0.0, svj = 0.0;
-          for (int n = 0; n < nv; ++n) {
-            const double cn = C[n * ld + a];
-            vj += (double)U[(size_t)n * m_cap * 4 + 4 * jr + c] * cn;
-            svj += (double)SU[(size_t)n * m_cap * 4 + 4 * jr + c] * cn;
-          }
-          e = evals[a];
-          wv = vj * svj;
-        }
-        A.eps[col * nu + a] = e;
-        A.w[col * nu + a] = wv;
-      }
-      if (A.keep) {
-        // pattern rows of V: blocks of the atom's own row, neighbour atom local index lcol
-        const int e0 = lrow[t0], e1 = lrow[t0 + 1];
-        const int64_t rbase = A.row_ptr[atom];
-        const int nrow = A.row_ptr[atom + 1] - A.row_ptr[atom];
-        // zero the whole output row first (blocks outside the cluster stay zero)
-        for (int i = threadIdx.x; i < nrow * 4 * nu; i += blockDim.x) {
-          const int k = i / (4 * nu), rem = i % (4 * nu);
-          A.vp[((A.blk_off[widx] + k) * 16 + c * 4) * (int64_t)nu + rem] = 0.0;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < (e1 - e0) * 4 * nu; i += blockDim.x) {
-          const int e = e0 + i / (4 * nu), rem = i % (4 * nu), r = rem / nu, a = rem % nu;
-          const int k = (int)(lblk[e] - rbase);
-          double v = 0.0;
-          if (ok && a < nv) {
-            const int row = 4 * lcol[e] + r;
-            for (int n = 0; n < nv; ++n) v += (double)U[(size_t)n * m_cap * 4 + 4 * row + c] * C[n * ld + a];
-          }
-          A.vp[((A.blk_off[widx] + k) * 16 + c * 4 + r) * (int64_t)nu + a] = v;
-        }
-        if (threadIdx.x == 0 && c == 0) {
-          int sk = -1;
-          for (int e = e0; e < e1; ++e)
-            if (lcol[e] == t0) sk = (int)(lblk[e] - rbase);
-          A.self_k[widx] = sk;
-        }
-      }
-      __syncthreads();
     }
+    // ---- outputs of the four columns, all threads -----------------------------------------
+    const int e0 = lrow[t0], e1 = lrow[t0 + 1];
+    const int64_t rbase = A.row_ptr[atom];
+    const int nrow = A.row_ptr[atom + 1] - A.row_ptr[atom];
+    for (int i = threadIdx.x; i < 4 * nu; i += blockDim.x) {
+      A.eps[4 * widx * nu + i] = 0.0;
+      A.w[4 * widx * nu + i] = 0.0;
+    }
+    if (A.keep)
+      for (int i = threadIdx.x; i < nrow * 16 * nu; i += blockDim.x) A.vp[A.blk_off[widx] * 16 * nu + i] = 0.0;
+    __syncthreads();
+    // eps_alpha and w_alpha = V_{j alpha} (S V)_{j alpha}: thread per (column, alpha)
+    for (int i = threadIdx.x; i < 4 * nu; i += blockDim.x) {
+      const int c = i / nu, a = i % nu, nv = st.n[c];
+      if (!st.accept[c] || a >= nv) continue;
+      const double* Hm = RM + (size_t)c * rm_col;
+      const RedScratch wsc(const_cast<double*>(Hm) + (size_t)2 * nu * ld, nu);
+      const int jr = 4 * t0 + c;
+      T vj = 0, svj = 0;
+      for (int n = 0; n < nv; ++n) {
+        const T cn = (T)Hm[n * ld + a];
+        vj += U[(size_t)n * m_cap * 4 + 4 * jr + c] * cn;
+        svj += SU[(size_t)n * m_cap * 4 + 4 * jr + c] * cn;
+      }
+      const int ra = wsc.rank[a];
+      A.eps[(4 * widx + c) * nu + ra] = wsc.evals[a];
+      A.w[(4 * widx + c) * nu + ra] = (double)vj * (double)svj;
+    }
+    if (A.keep) {
+      // pattern rows of V = U C: thread per (column, pattern block, orbital row), alpha in chunks of 8
+      const int ne = e1 - e0;
+      for (int i = threadIdx.x; i < 16 * ne; i += blockDim.x) {
+        const int c = i / (4 * ne), rem = i % (4 * ne), e = e0 + rem / 4, r = rem % 4, nv = st.n[c];
+        if (!st.accept[c]) continue;
+        const double* Hm = RM + (size_t)c * rm_col;
+        const RedScratch wsc(const_cast<double*>(Hm) + (size_t)2 * nu * ld, nu);
+        const int k = (int)(lblk[e] - rbase);
+        const T* urow = U + 4 * (4 * (int)lcol[e] + r) + c;
+        double* out = A.vp + ((A.blk_off[widx] + k) * 16 + c * 4 + r) * (int64_t)nu;
+        for (int a0 = 0; a0 < nv; a0 += 8) {
+          T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+          for (int n = 0; n < nv; ++n) {
+            const T un = urow[(size_t)n * m_cap * 4];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[j] += un * (a0 + j < nv ? (T)Hm[n * ld + a0 + j] : (T)0);
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (a0 + j < nv) out[wsc.rank[a0 + j]] = (double)acc[j];
+        }
+      }
+      if (threadIdx.x == 0) {
+        int sk = -1;
+        for (int e = e0; e < e1; ++e)
+          if (lcol[e] == t0) sk = (int)(lblk[e] - rbase);
+        A.self_k[widx] = sk;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -899,11 +1063,22 @@ void fill_system_args(Args<TV>& A, const mka_system* s) {
   A.cell_atoms = s->cells.atoms;
 }
 
-size_t dyn_smem_bytes(int nu, int lnnz_cap) {
-  size_t off = (size_t)(2 * kMaxCl + 1 + 2 * lnnz_cap) * sizeof(int);
-  off = (off + 15) & ~(size_t)15;
+// Dynamic shared memory of atoms_kernel: cluster list and local pattern, then one region that
+// holds three [m_cap][4] work vectors during CG and the basis, and the four columns' reduced
+// matrices (H_r / C, S_r / L and scratch) afterwards.
+size_t dyn_smem_bytes(int nu, int lnnz_cap, int mcap, size_t elem) {
+  size_t off = (size_t)(2 * kMaxCl + 1 + lnnz_cap) * sizeof(int) + (size_t)lnnz_cap * sizeof(uint16_t);
+  off = align_up(off, 16);
   const int ld = nu + 1;
-  return off + sizeof(double) * ((size_t)4 * nu * ld + nu + 4 * ((nu + 1) / 2 + 1));
+  const size_t vec = (size_t)3 * mcap * 4 * elem;
+  const size_t red = sizeof(double) * 4 * ((size_t)2 * nu * ld + red_scratch_doubles(nu));
+  return off + std::max(vec, red);
+}
+
+// Per-CTA global work slot: U and S U ([nu][m_cap][4]) and s_j ([m_cap][4]) in the arithmetic
+// type, then H_r and S_r of the four columns (FP64, nu x nu each).
+size_t slot_bytes_for(int nu, int mcap, size_t elem) {
+  return align_up(elem * ((size_t)2 * nu + 1) * mcap * 4, 256) + align_up(sizeof(double) * 8 * (size_t)nu * nu, 256);
 }
 
 template <typename TV, typename T>
@@ -931,7 +1106,7 @@ mka_status run_columns(mka_system* sys, mka_result* res, const mka_solve_params*
   A.blk_off = res->d_blk_off;
   A.self_k = res->d_self;
 
-  const size_t smem = dyn_smem_bytes(A.nu, A.lnnz_cap);
+  const size_t smem = dyn_smem_bytes(A.nu, A.lnnz_cap, A.mcap, sizeof(T));
   auto kern = atoms_kernel<TV, T>;
   MKA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, sms = 0, per_sm = 0;
@@ -940,8 +1115,7 @@ mka_status run_columns(mka_system* sys, mka_result* res, const mka_solve_params*
   MKA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
   if (per_sm < 1) return fail(MKA_ERR_INVALID_ARG, "per-atom working set does not fit in shared memory");
   const int64_t slots = std::min<int64_t>(res->n_sel, (int64_t)sms * per_sm);
-  A.slot_bytes = sizeof(T) * ((size_t)3 * A.nu + 7) * A.mcap * 4;
-  A.slot_bytes = (A.slot_bytes + 255) & ~(size_t)255;
+  A.slot_bytes = slot_bytes_for(A.nu, A.mcap, sizeof(T));
   char* scratch = nullptr;
   int* counter = nullptr;
   MKA_CUDA_TRY(cudaMallocAsync(&scratch, A.slot_bytes * slots + 256, st));
@@ -1050,7 +1224,7 @@ mka_status run_columns_static(const mka_system* sys, const int64_t* h_atoms, int
   A.keep = 0;
   // layout: [work counter | 256 B] [atom ids | rounded to 256 B] [per-CTA slots]
   const size_t sel_bytes = ((size_t)n_sel * sizeof(int64_t) + 255) & ~(size_t)255;
-  A.slot_bytes = (sizeof(double) * ((size_t)3 * A.nu + 7) * A.mcap * 4 + 255) & ~(size_t)255;
+  A.slot_bytes = slot_bytes_for(A.nu, A.mcap, sizeof(double));
   const size_t fixed = 256 + sel_bytes;
   if (fixed + A.slot_bytes > (size_t)MKA_STATIC_SCRATCH_BYTES)
     return fail(MKA_ERR_INVALID_ARG,
@@ -1059,7 +1233,7 @@ mka_status run_columns_static(const mka_system* sys, const int64_t* h_atoms, int
                     std::to_string((size_t)MKA_STATIC_SCRATCH_BYTES) +
                     " B; pass fewer atoms, a smaller p + q or a smaller max_cluster_atoms");
   const int64_t slots_fit = (int64_t)(((size_t)MKA_STATIC_SCRATCH_BYTES - fixed) / A.slot_bytes);
-  const size_t smem = dyn_smem_bytes(A.nu, A.lnnz_cap);
+  const size_t smem = dyn_smem_bytes(A.nu, A.lnnz_cap, A.mcap, sizeof(double));
   auto kern = atoms_kernel<TV, double>;
   MKA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, sms = 0, per_sm = 0;

@@ -259,3 +259,37 @@ def test_global_spmv(lib):
                     np.testing.assert_allclose(yf.double().cpu().numpy(), A @ x, rtol=0, atol=2e-5)
         finally:
             mka.mka_system_destroy(s)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp32"])
+def test_mixed_form_against_oracle_on_stored_values(lib, storage):
+    """Mixed form (FP32 products, CG and basis; FP64 cross-thread sums, reduced solve and mu):
+    |d rho| <= 1e-6 and |d E| <= 1e-5 eV/atom against the oracle run on the same stored values."""
+    mka = lib
+    w = WORKLOADS["diamond512"]
+    pos, box = workload_positions(w)
+    atoms = np.array([0, 1, 50, 99, 222, 301, 444, 511], dtype=np.int64)
+    ores = solve_atoms_parallel(pos, box, w.sk, w.R, atoms, w.p, w.q, storage=storage)
+    s = mka.mka_build_system(pos, box, w.sk, storage, cluster_radius=w.R)
+    try:
+        res, lv = gpu_solve(mka, s, atoms, w.p, w.q, cg_tol=1e-7, arith="mixed")
+        assert np.all(lv["status"] == 0)
+        oe, ow = osys.stack_eps_w(ores)
+        print(f"mixed {storage}: max|d eps| {np.abs(lv['eps'] - oe).max():.2e}  max|d w| {np.abs(lv['w'] - ow).max():.2e}")
+        # individual Ritz values with tiny weight move under a 1e-7 change of the subspace without
+        # touching rho; the gates are rho, E and mu below, eps and w are only bounded loosely
+        assert np.abs(lv["eps"] - oe).max() < 1e-2 and np.abs(lv["w"] - ow).max() < 1e-3
+        for mu in (0.3, 1.9):
+            rho, e, n = gpu_density(mka, s, res, mu, w.kT)
+            orho, oe_band, on = osys.density(ores, mu, w.kT)
+            drho = np.abs(rho - np.concatenate(orho)).max()
+            de = abs(e - oe_band) / len(atoms)
+            print(f"mixed {storage} mu={mu}: max|d rho| {drho:.2e}  |d E| {de:.2e} eV/atom")
+            assert drho <= 1e-6 and de <= 1e-5
+        n_e = w.electrons_per_atom * len(atoms)
+        dmu = abs(mka.mka_find_mu(res, n_e, w.kT) - osys.find_mu(ores, n_e, w.kT))
+        print(f"mixed {storage}: |d mu| {dmu:.2e} eV")
+        assert dmu < 1e-4
+        mka.mka_result_destroy(res)
+    finally:
+        mka.mka_system_destroy(s)
