@@ -244,6 +244,62 @@ mka_status mka_density_energy(mka_system* sys, mka_result* res, double mu, doubl
  * [n_blocks][4][4][2]. Needs keep_vectors = 1. */
 mka_status mka_greens(mka_system* sys, mka_result* res, double z_re, double z_im, double* g_out);
 
+/* ---- persistent, graph-captured batches ---------------------------------- */
+
+/* Launch shape of the per-atom kernel. */
+typedef struct {
+  int threads;        /* CTA size: 128, 256 or 512 (0 = 256) */
+  int ctas_per_sm;    /* cap on resident CTAs per SM (0 = as many as fit) */
+  int order_by_size;  /* 1: the work queue takes atoms by descending cluster size */
+} mka_tuning;
+
+typedef struct mka_plan mka_plan; /* every buffer of one batch of the work flow, plus its CUDA graphs */
+
+/* A plan for batches of up to `max_atoms` atoms of `sys` (4 columns each): the
+ * whole work flow of Eq. EQ-WORK-FLOW for one batch (the per-column brace with
+ * kept pattern rows, mu by bisection over the batch's columns, rho and the band
+ * energy) with every buffer allocated here, once. `tune` may be NULL (defaults,
+ * or pass the result of mka_autotune). The plan computes the largest cluster of
+ * the whole system once, to size its work slots. Work runs on `stream`. */
+mka_status mka_plan_create(mka_system* sys, int64_t max_atoms, const mka_solve_params* prm,
+                           const mka_tuning* tune, void* stream, mka_plan** out);
+
+/* Run one batch: `atoms` (host, n_sel <= max_atoms) are staged in pinned memory
+ * and the batch is enqueued as one CUDA graph (captured the first time this
+ * (n_sel, n_electrons, kT, rho_out) combination is seen, replayed afterwards):
+ * copy-in, optional ordering by cluster size, the persistent per-atom kernel,
+ * 64 device bisection steps for mu (bracket as mka_find_mu, tolerance 1e-12 eV),
+ * rho into `rho_out` (device, [n_blocks][4][4] as in mka_density_energy, may be
+ * NULL) and the band energy. Returns without waiting for the GPU; the call waits
+ * only for the previous batch to have read the staging buffer. */
+mka_status mka_plan_run(mka_plan* plan, const int64_t* atoms, int64_t n_sel, double n_electrons, double kT,
+                        double* rho_out);
+
+/* mu, band energy 2 sum_j sum_i rho_ij H_ji and electron count 2 sum f w of the
+ * last batch (host outputs, any may be NULL); synchronises the plan's stream. */
+mka_status mka_plan_scalars(mka_plan* plan, double* mu, double* e_band, double* n_elec);
+
+/* The plan's result object (levels, weights, status and kept rows of the last
+ * batch), borrowed: valid until the next run or mka_plan_destroy, never
+ * destroyed by the caller. Usable with mka_result_copy_levels, mka_greens and
+ * mka_density_energy (another mu). */
+mka_status mka_plan_result(mka_plan* plan, mka_result** res);
+
+/* The plan's launch shape, grid size and resident CTAs per SM in use. */
+mka_status mka_plan_info(const mka_plan* plan, mka_tuning* tune, int* grid, int* ctas_per_sm_used);
+
+void mka_plan_destroy(mka_plan* plan);
+
+/* Choose a launch shape for `prm` on this GPU: each candidate (threads 128/256/
+ * 512, resident CTAs per SM max/1/2, ordering by cluster size off/on) that fits
+ * runs the sample batch (host atoms) three times through a plan, the fastest of
+ * the last two timings wins. With `cache_path` (a JSON file, NULL = none) the
+ * choice is looked up first under a key of GPU name, storage, arithmetic, p+q,
+ * the sample's largest cluster (rounded down to 16) and the sample size, and
+ * stored there after a search. */
+mka_status mka_autotune(mka_system* sys, const mka_solve_params* prm, const int64_t* sample, int64_t n_sample,
+                        double n_electrons, double kT, const char* cache_path, void* stream, mka_tuning* out);
+
 /* ---- accounting ---------------------------------------------------------- */
 
 /* Number of CUDA kernels this library has launched since it was loaded (all

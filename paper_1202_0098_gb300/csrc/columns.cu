@@ -43,8 +43,7 @@
 namespace mka {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+constexpr int kMaxWarps = 16;   // CTAs of up to 512 threads
 constexpr int kMaxCl = MKA_MAX_CLUSTER_ATOMS;  // power of two (bitonic sort size bound)
 static_assert((kMaxCl & (kMaxCl - 1)) == 0, "cluster cap must be a power of two");
 
@@ -100,6 +99,7 @@ struct Args {
   const int32_t* cell_atoms;
   // work
   const int64_t* sel;
+  const int32_t* order;   // optional work order (selection indices), NULL = selection order
   int64_t n_sel;
   int* work_counter;
   // method
@@ -144,7 +144,7 @@ __device__ __forceinline__ void cta_sum4(double a[4], double* red, double* out) 
   __syncthreads();
   if (threadIdx.x < 4) {
     double s = 0;
-    for (int k = 0; k < kWarps; ++k) s += red[k * 4 + threadIdx.x];
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k * 4 + threadIdx.x];
     out[threadIdx.x] = s;
   }
   __syncthreads();
@@ -193,7 +193,7 @@ __device__ int gather_cluster(const Args<TV>& A, int64_t a, int* cl, int* cnt) {
   const int nz = cell_range(cell_coord(pz, A.cell_len[2], A.ncell[2]), A.ncell[2], rz);
   const int ncells = nx * ny * nz;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int ci = wid; ci < ncells; ci += kWarps) {
+  for (int ci = wid; ci < ncells; ci += (int)(blockDim.x >> 5)) {
     const int ix = ci / (ny * nz), iy = (ci / nz) % ny, iz = ci % nz;
     const int c = (rx[ix] * A.ncell[1] + ry[iy]) * A.ncell[2] + rz[iz];
     const int s0 = A.cell_start[c], s1 = A.cell_start[c + 1];
@@ -580,7 +580,7 @@ __device__ void gs_sweep(const T* U, const T* SU, const T* L, const T* KV, const
                          bool do_coef, const AtomState& st, double* coef, double* HS, int nu) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const bool proj = st.proj_any;
-  for (int mm = wid; mm < nmax; mm += kWarps) {
+  for (int mm = wid; mm < nmax; mm += (int)(blockDim.x >> 5)) {
     const T* su = SU + (size_t)mm * m_cap * 4;
     const T* u = U + (size_t)mm * m_cap * 4;
     T pc[4] = {0, 0, 0, 0}, ph[4] = {0, 0, 0, 0}, ps[4] = {0, 0, 0, 0};
@@ -623,11 +623,11 @@ __device__ void gs_sweep(const T* U, const T* SU, const T* L, const T* KV, const
   __syncthreads();
 }
 
-template <typename TV, typename T>
-__global__ void __launch_bounds__(kThreads) atoms_kernel(const Args<TV> A) {
+template <typename TV, typename T, int NT>
+__global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ AtomState st;
-  __shared__ double red[2 * kWarps * 4];
+  __shared__ double red[2 * kMaxWarps * 4];
   __shared__ double sums[4];
   __shared__ double coef[MKA_MAX_NU * 4];
   __shared__ int64_t cur_atom;
@@ -661,8 +661,8 @@ __global__ void __launch_bounds__(kThreads) atoms_kernel(const Args<TV> A) {
       cur_atom = w;
     }
     __syncthreads();
-    const int64_t widx = cur_atom;
-    if (widx >= A.n_sel) break;
+    if (cur_atom >= A.n_sel) break;
+    const int64_t widx = A.order ? (int64_t)A.order[cur_atom] : cur_atom;
     const int64_t atom = A.sel[widx];
 
     // ---- 1. cluster ----------------------------------------------------------------
@@ -1081,56 +1081,71 @@ size_t slot_bytes_for(int nu, int mcap, size_t elem) {
   return align_up(elem * ((size_t)2 * nu + 1) * mcap * 4, 256) + align_up(sizeof(double) * 8 * (size_t)nu * nu, 256);
 }
 
-template <typename TV, typename T>
-mka_status run_columns(mka_system* sys, mka_result* res, const mka_solve_params* prm, int max_cl,
-                       cudaStream_t st) {
-  Args<TV> A{};
-  fill_system_args(A, sys);
-  A.sel = res->d_sel;
-  A.n_sel = res->n_sel;
-  A.p = prm->p;
-  A.q = prm->q;
-  A.nu = prm->p + prm->q;
-  A.cg_tol = prm->cg_tol;
-  A.cg_maxit = prm->cg_maxit;
-  A.tau = 1e-10;
-  A.mcap = 4 * std::max(1, std::min(max_cl, kMaxCl));
-  A.lnnz_cap = std::max(1, std::min(max_cl, kMaxCl) * std::max(1, sys->max_row_blocks));
-  A.eps = res->d_eps;
-  A.w = res->d_w;
-  A.nu_eff = res->d_nu_eff;
-  A.cg_iters = res->d_cg_iters;
-  A.status = res->d_status;
-  A.keep = res->keep;
-  A.vp = res->d_vp;
-  A.blk_off = res->d_blk_off;
-  A.self_k = res->d_self;
-
-  const size_t smem = dyn_smem_bytes(A.nu, A.lnnz_cap, A.mcap, sizeof(T));
-  auto kern = atoms_kernel<TV, T>;
-  MKA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+template <typename TV, typename T, int NT>
+mka_status config_t(const mka_system* sys, int nu, int max_cl, int ctas_per_sm, AtomsConfig* out) {
+  AtomsConfig cf{};
+  cf.threads = NT;
+  cf.mcap = 4 * std::max(1, std::min(max_cl, kMaxCl));
+  cf.lnnz_cap = std::max(1, std::min(max_cl, kMaxCl) * std::max(1, sys->max_row_blocks));
+  cf.smem = dyn_smem_bytes(nu, cf.lnnz_cap, cf.mcap, sizeof(T));
+  cf.slot_bytes = slot_bytes_for(nu, cf.mcap, sizeof(T));
+  auto kern = atoms_kernel<TV, T, NT>;
+  MKA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem));
   int dev = 0, sms = 0, per_sm = 0;
   MKA_CUDA_TRY(cudaGetDevice(&dev));
   MKA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  MKA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+  MKA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, cf.smem));
   if (per_sm < 1) return fail(MKA_ERR_INVALID_ARG, "per-atom working set does not fit in shared memory");
-  const int64_t slots = std::min<int64_t>(res->n_sel, (int64_t)sms * per_sm);
-  A.slot_bytes = slot_bytes_for(A.nu, A.mcap, sizeof(T));
-  char* scratch = nullptr;
-  int* counter = nullptr;
-  MKA_CUDA_TRY(cudaMallocAsync(&scratch, A.slot_bytes * slots + 256, st));
-  MKA_CUDA_TRY(cudaMallocAsync(&counter, sizeof(int), st));
-  MKA_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
-  A.scratch = scratch;
-  A.work_counter = counter;
-  kern<<<(unsigned)slots, kThreads, smem, st>>>(A);
-  count_launches();
-  cudaError_t e = cudaGetLastError();
-  cudaFreeAsync(scratch, st);
-  cudaFreeAsync(counter, st);
-  if (e != cudaSuccess) return cuda_fail(e, "atoms_kernel launch");
+  if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
+  cf.per_sm = per_sm;
+  cf.grid_max = sms * per_sm;
+  *out = cf;
   return MKA_OK;
 }
+
+template <typename TV, typename T, int NT>
+mka_status launch_t(const mka_system* sys, const AtomsConfig& cf, const AtomsLaunchArgs& a, cudaStream_t st) {
+  Args<TV> A{};
+  fill_system_args(A, sys);
+  A.sel = a.sel;
+  A.order = a.order;
+  A.n_sel = a.n_sel;
+  A.work_counter = a.counter;
+  A.p = a.p;
+  A.q = a.q;
+  A.nu = a.p + a.q;
+  A.cg_tol = a.cg_tol;
+  A.cg_maxit = a.cg_maxit;
+  A.tau = 1e-10;
+  A.scratch = a.scratch;
+  A.slot_bytes = cf.slot_bytes;
+  A.mcap = cf.mcap;
+  A.lnnz_cap = cf.lnnz_cap;
+  A.eps = a.eps;
+  A.w = a.w;
+  A.nu_eff = a.nu_eff;
+  A.cg_iters = a.cg_iters;
+  A.status = a.status;
+  A.keep = a.keep;
+  A.vp = a.vp;
+  A.blk_off = a.blk_off;
+  A.self_k = a.self_k;
+  atoms_kernel<TV, T, NT><<<(unsigned)a.grid, NT, cf.smem, st>>>(A);
+  count_launches();
+  MKA_CUDA_TRY(cudaGetLastError());
+  return MKA_OK;
+}
+
+// Dispatch on (storage type, arithmetic, CTA size).
+#define MKA_DISPATCH_T(CALL, TV, T, threads)        \
+  ((threads) == 128 ? CALL(TV, T, 128) : (threads) == 512 ? CALL(TV, T, 512) : CALL(TV, T, 256))
+#define MKA_DISPATCH(CALL, storage, mixed, threads)                                                        \
+  ((storage) == MKA_FP64 ? ((mixed) ? MKA_DISPATCH_T(CALL, double, float, threads)                         \
+                                    : MKA_DISPATCH_T(CALL, double, double, threads))                       \
+   : (storage) == MKA_MIXED_FP32 ? ((mixed) ? MKA_DISPATCH_T(CALL, float, float, threads)                  \
+                                            : MKA_DISPATCH_T(CALL, float, double, threads))                \
+   : ((mixed) ? MKA_DISPATCH_T(CALL, __nv_bfloat16, float, threads)                                        \
+              : MKA_DISPATCH_T(CALL, __nv_bfloat16, double, threads)))
 
 }  // namespace
 
@@ -1148,20 +1163,57 @@ mka_status launch_cluster_sizes(const mka_system* sys, const int64_t* d_sel, int
   return MKA_OK;
 }
 
+mka_status atoms_config(const mka_system* sys, int nu, int arith, int max_cl, int threads, int ctas_per_sm,
+                        AtomsConfig* out) {
+  const bool mixed = arith != MKA_FP64;
+#define MKA_CFG(TV, T, NT) config_t<TV, T, NT>(sys, nu, max_cl, ctas_per_sm, out)
+  return MKA_DISPATCH(MKA_CFG, sys->storage, mixed, threads);
+#undef MKA_CFG
+}
+
+mka_status atoms_launch(const mka_system* sys, int arith, const AtomsConfig& cf, const AtomsLaunchArgs& a,
+                        cudaStream_t st) {
+  const bool mixed = arith != MKA_FP64;
+#define MKA_LAUNCH(TV, T, NT) launch_t<TV, T, NT>(sys, cf, a, st)
+  return MKA_DISPATCH(MKA_LAUNCH, sys->storage, mixed, cf.threads);
+#undef MKA_LAUNCH
+}
+
 mka_status launch_columns(mka_system* sys, mka_result* res, const mka_solve_params* prm, int max_cl,
                           cudaStream_t st) {
-  const bool mixed = prm->arith != MKA_FP64;
-  switch (sys->storage) {
-    case MKA_FP64:
-      return mixed ? run_columns<double, float>(sys, res, prm, max_cl, st)
-                   : run_columns<double, double>(sys, res, prm, max_cl, st);
-    case MKA_MIXED_FP32:
-      return mixed ? run_columns<float, float>(sys, res, prm, max_cl, st)
-                   : run_columns<float, double>(sys, res, prm, max_cl, st);
-    default:
-      return mixed ? run_columns<__nv_bfloat16, float>(sys, res, prm, max_cl, st)
-                   : run_columns<__nv_bfloat16, double>(sys, res, prm, max_cl, st);
-  }
+  AtomsConfig cf{};
+  mka_status s = atoms_config(sys, prm->p + prm->q, prm->arith, max_cl, 256, 0, &cf);
+  if (s) return s;
+  const int64_t grid = std::min<int64_t>(res->n_sel, cf.grid_max);
+  char* scratch = nullptr;
+  int* counter = nullptr;
+  MKA_CUDA_TRY(cudaMallocAsync(&scratch, cf.slot_bytes * grid + 256, st));
+  MKA_CUDA_TRY(cudaMallocAsync(&counter, sizeof(int), st));
+  MKA_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
+  AtomsLaunchArgs a{};
+  a.sel = res->d_sel;
+  a.order = nullptr;
+  a.n_sel = res->n_sel;
+  a.p = prm->p;
+  a.q = prm->q;
+  a.cg_tol = prm->cg_tol;
+  a.cg_maxit = prm->cg_maxit;
+  a.eps = res->d_eps;
+  a.w = res->d_w;
+  a.nu_eff = res->d_nu_eff;
+  a.cg_iters = res->d_cg_iters;
+  a.status = res->d_status;
+  a.keep = res->keep;
+  a.vp = res->d_vp;
+  a.blk_off = res->d_blk_off;
+  a.self_k = res->d_self;
+  a.scratch = scratch;
+  a.counter = counter;
+  a.grid = (int)grid;
+  s = atoms_launch(sys, prm->arith, cf, a, st);
+  cudaFreeAsync(scratch, st);
+  cudaFreeAsync(counter, st);
+  return s;
 }
 
 }  // namespace mka
@@ -1198,61 +1250,48 @@ mka_status static_scratch_address(void** out) {
   return MKA_OK;
 }
 
-template <typename TV>
 mka_status run_columns_static(const mka_system* sys, const int64_t* h_atoms, int64_t n_sel, int p, int q,
                               double cg_tol, int cg_maxit, int max_cl, double* eps, double* w, int32_t* nu_eff,
                               int32_t* cg_iters, int32_t* status, cudaStream_t st) {
   char* base = nullptr;
   mka_status s = static_scratch_address(reinterpret_cast<void**>(&base));
   if (s) return s;
-  Args<TV> A{};
-  fill_system_args(A, sys);
-  A.n_sel = n_sel;
-  A.p = p;
-  A.q = q;
-  A.nu = p + q;
-  A.cg_tol = cg_tol;
-  A.cg_maxit = cg_maxit;
-  A.tau = 1e-10;
-  A.mcap = 4 * max_cl;
-  A.lnnz_cap = std::max(1, max_cl * std::max(1, sys->max_row_blocks));
-  A.eps = eps;
-  A.w = w;
-  A.nu_eff = nu_eff;
-  A.cg_iters = cg_iters;
-  A.status = status;
-  A.keep = 0;
+  AtomsConfig cf{};
+  s = atoms_config(sys, p + q, MKA_FP64, max_cl, 256, 0, &cf);
+  if (s) return s;
   // layout: [work counter | 256 B] [atom ids | rounded to 256 B] [per-CTA slots]
-  const size_t sel_bytes = ((size_t)n_sel * sizeof(int64_t) + 255) & ~(size_t)255;
-  A.slot_bytes = slot_bytes_for(A.nu, A.mcap, sizeof(double));
+  const size_t sel_bytes = align_up((size_t)n_sel * sizeof(int64_t), 256);
   const size_t fixed = 256 + sel_bytes;
-  if (fixed + A.slot_bytes > (size_t)MKA_STATIC_SCRATCH_BYTES)
+  if (fixed + cf.slot_bytes > (size_t)MKA_STATIC_SCRATCH_BYTES)
     return fail(MKA_ERR_INVALID_ARG,
-                "mka_solve_columns_static: one work slot (" + std::to_string(A.slot_bytes) + " B) plus the atom list (" +
+                "mka_solve_columns_static: one work slot (" + std::to_string(cf.slot_bytes) + " B) plus the atom list (" +
                     std::to_string(sel_bytes) + " B) exceeds the fixed scratch of " +
                     std::to_string((size_t)MKA_STATIC_SCRATCH_BYTES) +
                     " B; pass fewer atoms, a smaller p + q or a smaller max_cluster_atoms");
-  const int64_t slots_fit = (int64_t)(((size_t)MKA_STATIC_SCRATCH_BYTES - fixed) / A.slot_bytes);
-  const size_t smem = dyn_smem_bytes(A.nu, A.lnnz_cap, A.mcap, sizeof(double));
-  auto kern = atoms_kernel<TV, double>;
-  MKA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int dev = 0, sms = 0, per_sm = 0;
-  MKA_CUDA_TRY(cudaGetDevice(&dev));
-  MKA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  MKA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-  if (per_sm < 1) return fail(MKA_ERR_INVALID_ARG, "per-atom working set does not fit in shared memory");
-  const int64_t grid = std::min<int64_t>(std::min<int64_t>(n_sel, slots_fit), (int64_t)sms * per_sm);
-  A.work_counter = reinterpret_cast<int*>(base);
-  A.sel = reinterpret_cast<const int64_t*>(base + 256);
-  A.scratch = base + fixed;
+  const int64_t slots_fit = (int64_t)(((size_t)MKA_STATIC_SCRATCH_BYTES - fixed) / cf.slot_bytes);
+  const int64_t grid = std::min<int64_t>(std::min<int64_t>(n_sel, slots_fit), cf.grid_max);
+  AtomsLaunchArgs a{};
+  a.counter = reinterpret_cast<int*>(base);
+  a.sel = reinterpret_cast<const int64_t*>(base + 256);
+  a.scratch = base + fixed;
+  a.order = nullptr;
+  a.n_sel = n_sel;
+  a.p = p;
+  a.q = q;
+  a.cg_tol = cg_tol;
+  a.cg_maxit = cg_maxit;
+  a.eps = eps;
+  a.w = w;
+  a.nu_eff = nu_eff;
+  a.cg_iters = cg_iters;
+  a.status = status;
+  a.keep = 0;
+  a.grid = (int)grid;
   // The counter must start at zero; the atom list is copied in; slots need no clearing
   // (the kernel writes every slot entry before reading it).
   MKA_CUDA_TRY(cudaMemsetAsync(base, 0, 256, st));
   MKA_CUDA_TRY(cudaMemcpyAsync(base + 256, h_atoms, (size_t)n_sel * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-  kern<<<(unsigned)grid, kThreads, smem, st>>>(A);
-  count_launches();
-  MKA_CUDA_TRY(cudaGetLastError());
-  return MKA_OK;
+  return atoms_launch(sys, MKA_FP64, cf, a, st);
 }
 
 }  // namespace
@@ -1271,16 +1310,6 @@ extern "C" mka_status mka_solve_columns_static(const mka_system* sys, const int6
     return fail(MKA_ERR_INVALID_ARG, "max_cluster_atoms must be in [1, MKA_MAX_CLUSTER_ATOMS]");
   for (int64_t t = 0; t < n_sel; ++t)
     if (atoms[t] < 0 || atoms[t] >= sys->n_atoms) return fail(MKA_ERR_INVALID_ARG, "atom index out of range");
-  cudaStream_t st = (cudaStream_t)stream;
-  switch (sys->storage) {
-    case MKA_FP64:
-      return run_columns_static<double>(sys, atoms, n_sel, p, q, cg_tol, cg_maxit, max_cluster_atoms, eps, w, nu_eff,
-                                        cg_iters, status, st);
-    case MKA_MIXED_FP32:
-      return run_columns_static<float>(sys, atoms, n_sel, p, q, cg_tol, cg_maxit, max_cluster_atoms, eps, w, nu_eff,
-                                       cg_iters, status, st);
-    default:
-      return run_columns_static<__nv_bfloat16>(sys, atoms, n_sel, p, q, cg_tol, cg_maxit, max_cluster_atoms, eps, w,
-                                               nu_eff, cg_iters, status, st);
-  }
+  return run_columns_static(sys, atoms, n_sel, p, q, cg_tol, cg_maxit, max_cluster_atoms, eps, w, nu_eff, cg_iters,
+                            status, (cudaStream_t)stream);
 }

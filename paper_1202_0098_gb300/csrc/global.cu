@@ -132,12 +132,26 @@ __global__ void bisect_kernel(const double* eps, const double* w, int64_t n, dou
   }
 }
 
+// Bracket state of a stream-ordered bisection (no host round trip): target, kT, tolerance,
+// ticket cleared; the range kernel then sets lo / hi.
+__global__ void mu_init_kernel(MuState* S, unsigned* ticket, double target, double kT, double tol) {
+  S->target = target;
+  S->kT = kT;
+  S->tol = tol;
+  S->iters = 0;
+  *ticket = 0;
+}
+
+__global__ void mu_finish_kernel(const MuState* S, double* mu_out) { *mu_out = 0.5 * (S->lo + S->hi); }
+
 // rho / E: one CTA per selected atom, thread per (block k, c, r) of its row.
 __global__ void density_kernel(const double* vp, const double* eps, const int64_t* blk_off, const int32_t* self_k,
                                const int64_t* sel, const int32_t* row_ptr, const void* valH, int storage,
-                               int nu, double mu, double kT, double* rho, double* e_partial) {
+                               int nu, double mu_host, const double* mu_dev, double kT, double* rho,
+                               double* e_partial) {
   __shared__ double red[kRedThreads / 32];
   __shared__ double f[4 * MKA_MAX_NU];
+  const double mu = mu_dev ? *mu_dev : mu_host;
   const int64_t t = blockIdx.x;
   const int64_t atom = sel[t];
   const int nrow = row_ptr[atom + 1] - row_ptr[atom];
@@ -212,8 +226,10 @@ __global__ void sum_kernel(const double* x, int64_t n, double* out) {
   }
 }
 
-__global__ void count_kernel(const double* eps, const double* w, int64_t n, double mu, double kT, double* out) {
+__global__ void count_kernel(const double* eps, const double* w, int64_t n, double mu_host, const double* mu_dev,
+                             double kT, double* out) {
   __shared__ double part[kRedThreads];
+  const double mu = mu_dev ? *mu_dev : mu_host;
   double s = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
     if (w[i] != 0.0) s += fermi(eps[i], mu, kT) * w[i];
@@ -335,6 +351,35 @@ mka_status spmv_dispatch(const mka_system* s, const void* val, int x_dtype, cons
 
 }  // namespace
 
+size_t mu_buffer_bytes() { return sizeof(MuState) + sizeof(double) * 2 * kRedBlocks + 64; }
+
+mka_status find_mu_enqueue(const double* eps, const double* w, int64_t n, double n_electrons, double kT, double tol,
+                           int halvings, void* buf, double* mu_dev_out, cudaStream_t st) {
+  MuState* S = reinterpret_cast<MuState*>(buf);
+  double* partial = reinterpret_cast<double*>(S + 1);
+  unsigned* ticket = reinterpret_cast<unsigned*>(partial + 2 * kRedBlocks);
+  const int blocks = (int)std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, (n + kRedThreads - 1) / kRedThreads));
+  mu_init_kernel<<<1, 1, 0, st>>>(S, ticket, n_electrons, kT, tol);
+  eps_range_kernel<<<blocks, kRedThreads, 0, st>>>(eps, w, n, partial, ticket, S);
+  for (int i = 0; i < halvings; ++i) bisect_kernel<<<blocks, kRedThreads, 0, st>>>(eps, w, n, partial, ticket, S);
+  mu_finish_kernel<<<1, 1, 0, st>>>(S, mu_dev_out);
+  count_launches(3 + halvings);
+  MKA_CUDA_TRY(cudaGetLastError());
+  return MKA_OK;
+}
+
+mka_status density_enqueue(const mka_system* sys, const int64_t* sel, const int64_t* blk_off, const int32_t* self_k,
+                           const double* vp, const double* eps, const double* w, int64_t n_sel, int nu,
+                           const double* mu_dev, double kT, double* rho_out, double* tmp, cudaStream_t st) {
+  density_kernel<<<(unsigned)n_sel, 128, 0, st>>>(vp, eps, blk_off, self_k, sel, sys->d_row_ptr, sys->d_valH,
+                                                  sys->storage, nu, 0.0, mu_dev, kT, rho_out, tmp);
+  sum_kernel<<<1, kRedThreads, 0, st>>>(tmp, n_sel, tmp + n_sel);
+  count_kernel<<<1, kRedThreads, 0, st>>>(eps, w, 4 * n_sel * nu, 0.0, mu_dev, kT, tmp + n_sel + 1);
+  count_launches(3);
+  MKA_CUDA_TRY(cudaGetLastError());
+  return MKA_OK;
+}
+
 mka_status launch_find_mu(mka_result* res, double n_electrons, double kT, double tol, double* mu_out) {
   cudaStream_t st = res->stream;
   const int64_t n = res->n_cols * res->nu;
@@ -377,9 +422,10 @@ mka_status launch_density(mka_system* sys, mka_result* res, double mu, double kT
   MKA_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(double) * (res->n_sel + 2), st));
   density_kernel<<<(unsigned)res->n_sel, 128, 0, st>>>(res->d_vp, res->d_eps, res->d_blk_off, res->d_self,
                                                        res->d_sel, sys->d_row_ptr, sys->d_valH, sys->storage,
-                                                       res->nu, mu, kT, rho_out, tmp);
+                                                       res->nu, mu, nullptr, kT, rho_out, tmp);
   sum_kernel<<<1, kRedThreads, 0, st>>>(tmp, res->n_sel, tmp + res->n_sel);
-  count_kernel<<<1, kRedThreads, 0, st>>>(res->d_eps, res->d_w, res->n_cols * res->nu, mu, kT, tmp + res->n_sel + 1);
+  count_kernel<<<1, kRedThreads, 0, st>>>(res->d_eps, res->d_w, res->n_cols * res->nu, mu, nullptr, kT,
+                                          tmp + res->n_sel + 1);
   count_launches(3);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && (e_band || n_elec)) {

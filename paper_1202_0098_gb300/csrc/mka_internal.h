@@ -76,6 +76,44 @@ struct mka_result {
 
 namespace mka {
 
+// Configuration of the per-atom kernel for a system, subspace size, arithmetic and CTA size.
+struct AtomsConfig {
+  int threads = 256;       // CTA size
+  int per_sm = 0;          // resident CTAs per SM used
+  int grid_max = 0;        // SMs x per_sm
+  size_t smem = 0;         // dynamic shared memory per CTA
+  size_t slot_bytes = 0;   // global work slot per CTA
+  int mcap = 0;            // 4 x largest cluster
+  int lnnz_cap = 0;        // local block capacity
+};
+
+// Arguments of one launch of the per-atom kernel over a selection.
+struct AtomsLaunchArgs {
+  const int64_t* sel = nullptr;    // device selected atoms
+  const int32_t* order = nullptr;  // device work order (selection indices) or NULL
+  int64_t n_sel = 0;
+  int p = 0, q = 0;
+  double cg_tol = 0;
+  int cg_maxit = 0;
+  double* eps = nullptr;
+  double* w = nullptr;
+  int32_t* nu_eff = nullptr;
+  int32_t* cg_iters = nullptr;
+  int32_t* status = nullptr;
+  int keep = 0;
+  double* vp = nullptr;
+  const int64_t* blk_off = nullptr;
+  int32_t* self_k = nullptr;
+  char* scratch = nullptr;         // grid x slot_bytes
+  int* counter = nullptr;          // zero in stream order before the launch
+  int grid = 0;
+};
+
+mka_status atoms_config(const mka_system* sys, int nu, int arith, int max_cl, int threads, int ctas_per_sm,
+                        AtomsConfig* out);
+mka_status atoms_launch(const mka_system* sys, int arith, const AtomsConfig& cf, const AtomsLaunchArgs& a,
+                        cudaStream_t st);
+
 // Kernels launched from the C entry points (defined in the .cu files).
 mka_status launch_cluster_sizes(const mka_system* sys, const int64_t* d_sel, int64_t n_sel, int32_t* d_sizes,
                                 cudaStream_t st);
@@ -87,6 +125,14 @@ mka_status launch_density(mka_system* sys, mka_result* res, double mu, double kT
 mka_status launch_greens(mka_system* sys, mka_result* res, double z_re, double z_im, double* g_out);
 mka_status launch_spmv(const mka_system* sys, int which, int x_dtype, const void* x, void* y, int k,
                        cudaStream_t st);
+
+// Stream-ordered (no host synchronisation, no allocation) variants used by plans and graphs.
+size_t mu_buffer_bytes();
+mka_status find_mu_enqueue(const double* eps, const double* w, int64_t n, double n_electrons, double kT, double tol,
+                           int halvings, void* buf, double* mu_dev_out, cudaStream_t st);
+mka_status density_enqueue(const mka_system* sys, const int64_t* sel, const int64_t* blk_off, const int32_t* self_k,
+                           const double* vp, const double* eps, const double* w, int64_t n_sel, int nu,
+                           const double* mu_dev, double kT, double* rho_out, double* tmp, cudaStream_t st);
 
 size_t storage_bytes(int storage);
 

@@ -29,7 +29,8 @@ EXPORTED = [
     "mka_build_system", "mka_build_system_bsr", "mka_system_info", "mka_system_copy_bsr", "mka_cluster_sizes",
     "mka_system_destroy", "mka_spmv", "mka_solve_columns", "mka_solve_columns_static", "mka_result_info", "mka_result_copy_levels",
     "mka_result_device_levels", "mka_result_destroy", "mka_find_mu", "mka_density_energy", "mka_greens",
-    "mka_kernel_launches", "mka_last_error", "mka_status_string",
+    "mka_plan_create", "mka_plan_run", "mka_plan_scalars", "mka_plan_result", "mka_plan_info", "mka_plan_destroy",
+    "mka_autotune", "mka_kernel_launches", "mka_last_error", "mka_status_string",
 ]
 
 
@@ -42,6 +43,10 @@ class MkaError(RuntimeError):
 class mka_sk_params(C.Structure):
     _fields_ = [("Es", C.c_double), ("Ep", C.c_double), ("V", C.c_double * 4), ("Sv", C.c_double * 4),
                 ("d0", C.c_double), ("rc", C.c_double)]
+
+
+class mka_tuning(C.Structure):
+    _fields_ = [("threads", C.c_int), ("ctas_per_sm", C.c_int), ("order_by_size", C.c_int)]
 
 
 class mka_solve_params(C.Structure):
@@ -81,6 +86,12 @@ def load(path: str | None = None) -> C.CDLL:
         "mka_find_mu": [P, D, D, D, P],
         "mka_density_energy": [P, P, D, D, P, P, P],
         "mka_greens": [P, P, D, D, P],
+        "mka_plan_create": [P, I64, P, P, P, P],
+        "mka_plan_run": [P, P, I64, D, D, P],
+        "mka_plan_scalars": [P, P, P, P],
+        "mka_plan_result": [P, P],
+        "mka_plan_info": [P, P, P, P],
+        "mka_autotune": [P, P, P, I64, D, D, C.c_char_p, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -88,6 +99,8 @@ def load(path: str | None = None) -> C.CDLL:
         f.restype = C.c_int
     lib.mka_system_destroy.argtypes = [P]
     lib.mka_system_destroy.restype = None
+    lib.mka_plan_destroy.argtypes = [P]
+    lib.mka_plan_destroy.restype = None
     lib.mka_result_destroy.argtypes = [P]
     lib.mka_result_destroy.restype = None
     lib.mka_kernel_launches.argtypes = []
@@ -262,6 +275,60 @@ def mka_density_energy(sys, res, mu: float, kT: float, rho_ptr: int | None = Non
 
 def mka_greens(sys, res, z: complex, g_ptr: int):
     _check(load().mka_greens(sys, res, float(z.real), float(z.imag), C.c_void_p(g_ptr)), "mka_greens")
+
+
+def tuning(threads: int = 256, ctas_per_sm: int = 0, order_by_size: bool = False) -> mka_tuning:
+    t = mka_tuning()
+    t.threads, t.ctas_per_sm, t.order_by_size = threads, ctas_per_sm, int(order_by_size)
+    return t
+
+
+def mka_plan_create(sys, max_atoms: int, prm: mka_solve_params, tune: mka_tuning | None = None,
+                    stream: int = 0) -> C.c_void_p:
+    out = C.c_void_p()
+    _check(load().mka_plan_create(sys, int(max_atoms), C.byref(prm), C.byref(tune) if tune is not None else None,
+                                  C.c_void_p(stream), C.byref(out)), "mka_plan_create")
+    return out
+
+
+def mka_plan_run(plan, atoms: np.ndarray, n_electrons: float, kT: float, rho_ptr: int | None = None):
+    a = np.ascontiguousarray(atoms, dtype=np.int64)
+    _check(load().mka_plan_run(plan, _ptr(a), a.shape[0], float(n_electrons), float(kT),
+                               C.c_void_p(rho_ptr) if rho_ptr else None), "mka_plan_run")
+
+
+def mka_plan_scalars(plan) -> tuple[float, float, float]:
+    mu, e, n = C.c_double(), C.c_double(), C.c_double()
+    _check(load().mka_plan_scalars(plan, C.byref(mu), C.byref(e), C.byref(n)), "mka_plan_scalars")
+    return mu.value, e.value, n.value
+
+
+def mka_plan_result(plan) -> C.c_void_p:
+    out = C.c_void_p()
+    _check(load().mka_plan_result(plan, C.byref(out)), "mka_plan_result")
+    return out
+
+
+def mka_plan_info(plan) -> dict:
+    t, g, c = mka_tuning(), C.c_int(), C.c_int()
+    _check(load().mka_plan_info(plan, C.byref(t), C.byref(g), C.byref(c)), "mka_plan_info")
+    return {"threads": t.threads, "ctas_per_sm": t.ctas_per_sm, "order_by_size": t.order_by_size, "grid": g.value,
+            "ctas_per_sm_used": c.value}
+
+
+def mka_plan_destroy(plan):
+    if plan:
+        load().mka_plan_destroy(plan)
+
+
+def mka_autotune(sys, prm: mka_solve_params, sample: np.ndarray, n_electrons: float, kT: float,
+                 cache_path: str | None = None, stream: int = 0) -> mka_tuning:
+    a = np.ascontiguousarray(sample, dtype=np.int64)
+    out = mka_tuning()
+    _check(load().mka_autotune(sys, C.byref(prm), _ptr(a), a.shape[0], float(n_electrons), float(kT),
+                               cache_path.encode() if cache_path else None, C.c_void_p(stream), C.byref(out)),
+           "mka_autotune")
+    return out
 
 
 def mka_kernel_launches() -> int:
