@@ -42,11 +42,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="diamond10m")
-    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--form", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--storage", default=None, choices=[None, "fp64", "fp32", "bf16"])
     ap.add_argument("--batch", type=int, default=0, help="atoms per step (0: per form default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shape instead of the autotuner's")
     return ap.parse_args()
 
 
@@ -187,6 +189,75 @@ def cpu_baseline(w, pos, box, budget_s=20.0):
                       f"one spawn process per core"}
 
 
+def flops_split(m, nnz, nu, cg_it, n_pattern_rows):
+    """Algorithmic (vector-work, reduced-solve) FLOPs of one column; see the design doc section 6."""
+    total = column_flops(m, nnz, nu, cg_it, n_pattern_rows)
+    red = 12.3 * nu ** 3
+    return total - red, red
+
+
+def alu_roofline(f_vec, f_red, kernel_s, n_cols, form):
+    """Two-pipe ALU bound of the per-atom kernel: the vector work on the form's pipe, the reduced
+    solve on the FP64 pipe; the bound time is the larger of the two, frac = bound / measured."""
+    p_vec = FP64_PEAK_TFLOPS if form == "fp64" else FP32_PEAK_TFLOPS
+    t_vec = f_vec * n_cols / (p_vec * 1e12)
+    t_red = f_red * n_cols / (FP64_PEAK_TFLOPS * 1e12)
+    t_bound = t_vec + t_red if form == "fp64" else max(t_vec, t_red)
+    flops = (f_vec + f_red) * n_cols
+    achieved = flops / kernel_s / 1e12
+    peak = flops / t_bound / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "atoms_kernel",
+            "peak_source": ("derived: 152 SMs x 1.98 GHz x 2 x (FP64 2 | FP32 128 FMA/clk/SM); vector work on the "
+                            f"{'FP64' if form == 'fp64' else 'FP32'} pipe, reduced solve on the FP64 pipe, "
+                            f"bound = {'sum' if form == 'fp64' else 'max'} of the two times"),
+            "flops_per_column": {"vector": f_vec, "reduced_fp64": f_red}}
+
+
+def run_form(mka, torch, sysh, w, form, B, batch_atoms, steps, warmup, stream, tune_cache, rank, autotune=True,
+             compare=()):
+    """Time `steps` batches of one form through an autotuned plan (graph replay); returns timings + outputs."""
+    cg_tol = 1e-12 if form == "fp64" else 1e-7
+    prm = mka.solve_params(w.p, w.q, arith=form, cg_tol=cg_tol, keep_vectors=True)
+    sp = stream.cuda_stream
+    if autotune:
+        tune = mka.mka_autotune(sysh, prm, batch_atoms(0)[:min(B, 4096)], w.electrons_per_atom * min(B, 4096), w.kT,
+                                tune_cache, sp)
+    else:
+        tune = mka.tuning()
+    plan = mka.mka_plan_create(sysh, B, prm, tune, sp)
+    mrb = mka.mka_system_info(sysh)["max_row_blocks"]
+    rho = torch.empty(B * mrb * 16, dtype=torch.float64, device="cuda")
+    n_e = w.electrons_per_atom * B
+    for i in range(warmup):
+        mka.mka_plan_run(plan, batch_atoms(i), n_e, w.kT, rho.data_ptr())
+    torch.cuda.synchronize()
+    out = {"tuning": mka.mka_plan_info(plan)}
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kms, mus, ebs = [], [], []
+    launches0 = mka.mka_kernel_launches()
+    t0.record(stream)
+    for i in range(warmup, warmup + steps):
+        mka.mka_plan_run(plan, batch_atoms(i), n_e, w.kT, rho.data_ptr())
+        kms.append(mka.mka_plan_kernel_ms(plan))      # waits for this batch's kernel only
+    t1.record(stream)
+    torch.cuda.synchronize()
+    out["launches"] = mka.mka_kernel_launches() - launches0
+    out["ms"] = t0.elapsed_time(t1)
+    out["kernel_ms"] = kms
+    # outputs of the comparison batches (the same batch indices for every form), outside the timed region
+    for i in compare:
+        mka.mka_plan_run(plan, batch_atoms(i), n_e, w.kT, rho.data_ptr())
+        mu, e, _ = mka.mka_plan_scalars(plan)
+        mus.append(mu)
+        ebs.append(e)
+    lv = mka.mka_result_copy_levels(mka.mka_plan_result(plan), check=False)
+    out["mu"], out["e_band"], out["cg_iters"] = mus, ebs, float(lv["cg_iters"].mean())
+    out["bad_columns"] = int(np.sum((lv["status"] != 0) & (lv["status"] != 4)))
+    out["plan"], out["rho"], out["prm"] = plan, rho, prm
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -195,126 +266,113 @@ def main():
         return
     import torch
     import torch.distributed as dist
-    from paper_1202_0098_gb300 import mka
+    from paper_1202_0098_gb300 import build as mka_build, mka
 
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w = WORKLOADS[args.workload]
-    storage = args.storage or ("fp64" if args.form == "fp64" else "bf16")
-    B = args.batch or (8192 if args.form == "fp64" else 65536)
+    storage = args.storage or "bf16"
+    form = args.form
+    B = args.batch or 65536
     pos, box = workload_positions(w)
     N = pos.shape[0]
     t_build = time.perf_counter()
     sysh = mka.mka_build_system(pos, box, w.sk, storage, cluster_radius=w.R)
     t_build = time.perf_counter() - t_build
     stream = torch.cuda.current_stream()
-    sp = stream.cuda_stream
-    cg_tol = 1e-12 if args.form == "fp64" else 1e-7
-    prm = mka.solve_params(w.p, w.q, arith="fp64" if args.form == "fp64" else "mixed", cg_tol=cg_tol,
-                           keep_vectors=True)
+    tune_cache = os.path.join(mka_build.BUILD, "autotune.json")
     n_steps = args.warmup + args.steps
 
     def batch_atoms(i):
         start = ((rank * n_steps + i) * B) % N
-        return (np.arange(start, start + B, dtype=np.int64) % N)
+        return np.arange(start, start + B, dtype=np.int64) % N
 
-    def step(i, host=False):
-        atoms = batch_atoms(i)
-        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-        ev[0].record(stream)
-        res = mka.mka_solve_columns(sysh, atoms, prm, stream=sp)
-        ev[1].record(stream)
-        mu = mka.mka_find_mu(res, w.electrons_per_atom * B, w.kT)
-        nb = mka.mka_result_info(res)["n_blocks"]
-        rho = torch.empty(nb * 16, dtype=torch.float64, device="cuda")
-        e_band, n_el = mka.mka_density_energy(sysh, res, mu, w.kT, rho.data_ptr())
-        out = None
-        if host:
-            out = (rho.cpu(), mka.mka_result_copy_levels(res, check=False))
-        mka.mka_result_destroy(res)
-        return ev, mu, e_band, nb, out
-
-    for i in range(args.warmup):
-        step(i)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    t0.record(stream)
-    kevs, mus, ebs = [], [], []
-    launches0 = mka.mka_kernel_launches()
-    for i in range(args.warmup, n_steps):
-        ev, mu, eb, nb, _ = step(i)
-        kevs.append(ev)
-        mus.append(mu)
-        ebs.append(eb)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    launches = mka.mka_kernel_launches() - launches0
-    ms = t0.elapsed_time(t1)
+    compare = list(range(args.warmup, args.warmup + max(1, min(args.steps, 3))))
+    main_run = run_form(mka, torch, sysh, w, form, B, batch_atoms, args.steps, args.warmup, stream, tune_cache, rank,
+                        not args.no_autotune, compare)
+    ms = main_run["ms"]
     if world > 1:
         tt = torch.tensor([ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
-    cols_total = 4 * B * args.steps * world
-    value = cols_total / (ms / 1e3)
-    solve_ms = [a.elapsed_time(b) for a, b in kevs]
+    value = 4 * B * args.steps * world / (ms / 1e3)
 
-    # end to end through the public API with host buffers (host atoms in, rho and levels out)
+    # clocks during a second pass of the same timed batches
+    clocks = ClockSampler(local)
+    clocks.start()
+    plan = main_run["plan"]
+    n_e = w.electrons_per_atom * B
+    for i in range(args.warmup, n_steps):
+        mka.mka_plan_run(plan, batch_atoms(i), n_e, w.kT, main_run["rho"].data_ptr())
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+
+    # end to end through the public API with host buffers: host atoms in; mu, E, levels and rho out
     e2e = None
     if not args.no_e2e:
+        rho_h = torch.empty(main_run["rho"].numel(), dtype=torch.float64, pin_memory=True)
         torch.cuda.synchronize()
         te = time.perf_counter()
-        h2d = d2h = 0
-        cg_its = []
+        d2h = 0
         for i in range(args.warmup, n_steps):
-            ev, mu, eb, nb, out = step(i, host=True)
-            h2d += 8 * B + 8 * (B + 1)
-            d2h += out[0].numel() * 8 + 4 * B * w.nu * 8 * 2 + 4 * B * 4 * 3
-            cg_its.append(float(out[1]["cg_iters"].mean()))
+            mka.mka_plan_run(plan, batch_atoms(i), n_e, w.kT, main_run["rho"].data_ptr())
+            mka.mka_plan_scalars(plan)
+            lv = mka.mka_result_copy_levels(mka.mka_plan_result(plan), check=False)
+            nb = mka.mka_result_info(mka.mka_plan_result(plan))["n_blocks"]
+            rho_h[:nb * 16].copy_(main_run["rho"][:nb * 16])
+            d2h += nb * 16 * 8 + sum(v.nbytes for k, v in lv.items() if hasattr(v, "nbytes")) + 24
         torch.cuda.synchronize()
         te = time.perf_counter() - te
-        e2e = {"value": 4 * B * args.steps * world / te, "unit": "columns/s",
-               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+        e2e = {"value": 4 * B * args.steps * world / te, "unit": "columns/s", "h2d_bytes_per_step": 16 * B + 8,
+               "d2h_bytes_per_step": d2h // args.steps}
 
-    # roofline of the per-atom kernel: algorithmic FLOPs of the timed batches / its event time
+    # the FP64 form on the same stored values and batches: speed and agreement of mu / E
+    other = None
+    if form != "fp64" and not args.no_fp64_compare:
+        fsteps = max(1, min(args.steps, 3))
+        frun = run_form(mka, torch, sysh, w, "fp64", B, batch_atoms, fsteps, 1, stream, tune_cache, rank,
+                        not args.no_autotune, compare)
+        fval = 4 * B * fsteps / (frun["ms"] / 1e3)
+        de = max(abs(a - b) for a, b in zip(main_run["e_band"], frun["e_band"])) / B
+        dmu = max(abs(a - b) for a, b in zip(main_run["mu"], frun["mu"]))
+        other = {"form": "fp64", "value": fval, "unit": "columns/s", "steps": fsteps,
+                 "speedup_of_headline": value / world / fval, "compared_batches": len(compare),
+                 "max_abs_dE_eV_per_atom": de, "max_abs_dmu_eV": dmu,
+                 "tuning": frun["tuning"], "kernel_ms_mean": statistics.mean(frun["kernel_ms"])}
+        mka.mka_plan_destroy(frun["plan"])
+
+    # roofline of the per-atom kernel from its in-graph event time
     from scipy.spatial import cKDTree
     bsr = mka.mka_system_copy_bsr(sysh)
     tree = cKDTree(pos, boxsize=box)
-    cg_mean = statistics.mean(cg_its) if e2e else 20.0
-    flops = 0.0
+    fv = fr = 0.0
     for i in range(args.warmup, n_steps):
         atoms = batch_atoms(i)[::max(1, B // 256)]
         m_c, nnz_c = local_flops(tree, pos, bsr["row_ptr"], bsr["col"], atoms, w.R)
         rows = 4 * np.diff(bsr["row_ptr"])[atoms]
-        flops += column_flops(m_c, nnz_c, w.nu, cg_mean, rows).mean() * 4 * B
-    achieved = flops / (sum(solve_ms) / 1e3) / 1e12
-    peak = FP64_PEAK_TFLOPS if args.form == "fp64" else FP32_PEAK_TFLOPS
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "atoms_kernel",
-                "peak_source": "derived: 152 SMs x FMA/clk x 2 x 1.98 GHz (FP64 2, FP32 128 FMA/clk/SM)"}
+        a_v, a_r = flops_split(m_c, nnz_c, w.nu, main_run["cg_iters"], rows)
+        fv += float(np.mean(a_v)) / args.steps
+        fr += float(np.mean(a_r)) / args.steps
+    kernel_s = statistics.mean(main_run["kernel_ms"]) / 1e3
+    roofline = alu_roofline(fv, fr, kernel_s, 4 * B, form)
+    mka.mka_plan_destroy(plan)
     mka.mka_system_destroy(sysh)
 
     line = {"metric": "density-matrix columns/s", "value": value, "unit": "columns/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.form == "fp64" else "f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if form == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {N} atoms, {4 * N} columns, R={w.R} A, p=q={w.p}, "
-                                   f"kT={w.kT} eV, {args.form} form, {storage} storage",
-                       "atoms_per_step": B, "columns_per_step": 4 * B, "l2": "inputs larger than L2 "
-                       "(H,S of the whole system in HBM; each step a new batch of atoms)",
-                       "build_s": t_build},
-            "gpu_launches": launches, "clocks": clk, "e2e": e2e, "roofline": roofline,
-            "solve_ms_per_step": sum(solve_ms) / len(solve_ms), "cg_iters_mean": cg_mean, "mu_last": mus[-1],
-            "e_band_per_atom_last": ebs[-1] / B}
+                                   f"kT={w.kT} eV, {form} form, {storage}-stored H and S",
+                       "atoms_per_step": B, "columns_per_step": 4 * B,
+                       "step": "one graph-replayed batch: per-atom kernel, mu bisection over the batch, rho, E",
+                       "l2": "inputs larger than L2 (H,S of the whole system in HBM; each step a new batch of atoms)",
+                       "tuning": main_run["tuning"], "build_s": t_build},
+            "gpu_launches": main_run["launches"], "clocks": clk, "e2e": e2e, "roofline": roofline,
+            "kernel_ms_mean": statistics.mean(main_run["kernel_ms"]), "cg_iters_mean": main_run["cg_iters"],
+            "bad_columns": main_run["bad_columns"], "fp64_form": other,
+            "mu_first_compared": main_run["mu"][0], "e_band_per_atom_first_compared": main_run["e_band"][0] / B}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, pos, box)
     if rank == 0:

@@ -91,8 +91,10 @@ struct Args {
   const TV* valH;
   const TV* valS;
   const double* pos;
+  const float* posf;      // positions rounded to FP32, for the distance prefilter
   double box[3];
   double R2;
+  float pre_lo, pre_hi;   // FP32 prefilter: inside below pre_lo * R^2, outside above pre_hi * R^2
   int ncell[3];
   double cell_len[3];
   const int32_t* cell_start;
@@ -164,6 +166,28 @@ __device__ __forceinline__ int find_local(const int* cl, int n, int c) {
 
 __device__ __forceinline__ double min_image(double d, double L) { return d - L * rint(d / L); }
 
+// Is atom b within R of the point (px, py, pz) (minimum image)? An FP32 test decides every
+// candidate whose FP32 distance is clear of the boundary by more than its rounding error
+// (relative margin max(1e-3, 1e-5 L / R) on R^2); the rest get the exact FP64 test.
+__device__ __forceinline__ bool within_R(const double* pos, const float* posf, const double box[3], double R2,
+                                         float pre_lo, float pre_hi, int b, double px, double py, double pz,
+                                         float pxf, float pyf, float pzf) {
+  const float Lx = (float)box[0], Ly = (float)box[1], Lz = (float)box[2];
+  float fx = posf[3 * b] - pxf, fy = posf[3 * b + 1] - pyf, fz = posf[3 * b + 2] - pzf;
+  fx -= Lx * rintf(fx / Lx);
+  fy -= Ly * rintf(fy / Ly);
+  fz -= Lz * rintf(fz / Lz);
+  const float r2f = fx * fx + fy * fy + fz * fz;
+  const float R2f = (float)R2;
+  if (r2f < pre_lo * R2f) return true;
+  if (r2f > pre_hi * R2f) return false;
+  const double dx = pos[3 * b] - px - box[0] * rint((pos[3 * b] - px) / box[0]);
+  const double dy = pos[3 * b + 1] - py - box[1] * rint((pos[3 * b + 1] - py) / box[1]);
+  const double dz = pos[3 * b + 2] - pz - box[2] * rint((pos[3 * b + 2] - pz) / box[2]);
+  const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+  return r2 <= R2;
+}
+
 __device__ __forceinline__ int cell_range(int c, int n, int out[3]) {
   if (n < 3) {
     for (int i = 0; i < n; ++i) out[i] = i;
@@ -187,6 +211,7 @@ __device__ int gather_cluster(const Args<TV>& A, int64_t a, int* cl, int* cnt) {
   if (threadIdx.x == 0) *cnt = 0;
   __syncthreads();
   const double px = A.pos[3 * a], py = A.pos[3 * a + 1], pz = A.pos[3 * a + 2];
+  const float pxf = A.posf[3 * a], pyf = A.posf[3 * a + 1], pzf = A.posf[3 * a + 2];
   int rx[3], ry[3], rz[3];
   const int nx = cell_range(cell_coord(px, A.cell_len[0], A.ncell[0]), A.ncell[0], rx);
   const int ny = cell_range(cell_coord(py, A.cell_len[1], A.ncell[1]), A.ncell[1], ry);
@@ -199,11 +224,7 @@ __device__ int gather_cluster(const Args<TV>& A, int64_t a, int* cl, int* cnt) {
     const int s0 = A.cell_start[c], s1 = A.cell_start[c + 1];
     for (int k = s0 + lane; k < s1; k += 32) {
       const int b = A.cell_atoms[k];
-      const double dx = min_image(A.pos[3 * b] - px, A.box[0]);
-      const double dy = min_image(A.pos[3 * b + 1] - py, A.box[1]);
-      const double dz = min_image(A.pos[3 * b + 2] - pz, A.box[2]);
-      const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-      if (r2 <= A.R2) {
+      if (within_R(A.pos, A.posf, A.box, A.R2, A.pre_lo, A.pre_hi, b, px, py, pz, pxf, pyf, pzf)) {
         const int idx = atomicAdd(cnt, 1);
         if (idx < kMaxCl) cl[idx] = b;
       }
@@ -237,6 +258,23 @@ __device__ void sort_cluster(int* cl, int n) {
   }
 }
 
+// 16-byte (float) / 2 x 16-byte (double) access to one [row][4] entry of a work vector.
+__device__ __forceinline__ void ld4(const float* p, float v[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double v[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, float a0, float a1, float a2, float a3) {
+  *reinterpret_cast<float4*>(p) = make_float4(a0, a1, a2, a3);
+}
+__device__ __forceinline__ void st4(double* p, double a0, double a1, double a2, double a3) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a0, a1);
+  reinterpret_cast<double2*>(p)[1] = make_double2(a2, a3);
+}
+
 // y = A x on the cluster for the columns in `mask` (bit c = column c), rows 4t + i;
 // x, y are [m][4] in shared memory; other columns of y are left untouched.
 template <typename TV, typename T>
@@ -255,17 +293,16 @@ __device__ __forceinline__ void spmm4(const TV* __restrict__ val, const int* lro
       const T* xb = x + (size_t)lcol[e] * 16;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        a0 += v[k] * xb[4 * k + 0];
-        a1 += v[k] * xb[4 * k + 1];
-        a2 += v[k] * xb[4 * k + 2];
-        a3 += v[k] * xb[4 * k + 3];
+        T xk[4];
+        ld4(xb + 4 * k, xk);
+        a0 += v[k] * xk[0];
+        a1 += v[k] * xk[1];
+        a2 += v[k] * xk[2];
+        a3 += v[k] * xk[3];
       }
     }
     if (mask == 15) {
-      y[4 * r + 0] = a0;
-      y[4 * r + 1] = a1;
-      y[4 * r + 2] = a2;
-      y[4 * r + 3] = a3;
+      st4(y + 4 * r, a0, a1, a2, a3);
     } else {
       if (mask & 1) y[4 * r + 0] = a0;
       if (mask & 2) y[4 * r + 1] = a1;
@@ -577,7 +614,7 @@ __device__ bool warp_reduced_solve(double* Hm, double* Lm, int n, int ld, const 
 // S_r[mm][pn] = u_mm^T (S u_pn) written (with their mirror) to HS.
 template <typename T>
 __device__ void gs_sweep(const T* U, const T* SU, const T* L, const T* KV, const T* SV, int m, int m_cap, int nmax,
-                         bool do_coef, const AtomState& st, double* coef, double* HS, int nu) {
+                         bool do_coef, const AtomState& st, double* coef, T* coefT, double* HS, int nu) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const bool proj = st.proj_any;
   for (int mm = wid; mm < nmax; mm += (int)(blockDim.x >> 5)) {
@@ -608,7 +645,11 @@ __device__ void gs_sweep(const T* U, const T* SU, const T* L, const T* KV, const
     }
     if (lane < 4) {
       const int c = lane;
-      if (do_coef) coef[mm * 4 + c] = (st.active[c] && mm < st.n[c]) ? (double)pc[c] : 0.0;
+      if (do_coef) {
+        const bool use = st.active[c] && mm < st.n[c];
+        coef[mm * 4 + c] = use ? (double)pc[c] : 0.0;
+        coefT[mm * 4 + c] = use ? pc[c] : (T)0;
+      }
       if (proj && st.proj[c] && mm < st.n[c]) {
         const int pn = st.n[c] - 1;
         double* H = HS + (size_t)c * 2 * nu * nu;
@@ -630,6 +671,8 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
   __shared__ double red[2 * kMaxWarps * 4];
   __shared__ double sums[4];
   __shared__ double coef[MKA_MAX_NU * 4];
+  __shared__ T coefT[MKA_MAX_NU * 4];    // the same coefficients in the arithmetic type
+  __shared__ T scal[12];                 // CG alpha [0..4), CG beta [4..8), 1 / beta of the basis [8..12)
   __shared__ int64_t cur_atom;
   __shared__ int cnt;
 
@@ -753,12 +796,13 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
           }
         }
         st.alpha[c] = a;
+        scal[c] = (T)a;
       }
       __syncthreads();
       for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
         const int c = i & 3;
         if (st.cg_active[c]) {
-          const T a = (T)st.alpha[c];
+          const T a = scal[c];
           SJ[i] += a * P[i];
           R[i] -= a * AP[i];
         }
@@ -769,6 +813,7 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
         const int c = threadIdx.x;
         if (st.cg_active[c]) {
           st.beta_cg[c] = sums[c] / st.rr[c];
+          scal[4 + c] = (T)st.beta_cg[c];
           st.rr[c] = sums[c];
           st.it[c] += 1;
           if (sqrt(sums[c]) <= A.cg_tol) st.cg_active[c] = 0;
@@ -777,7 +822,7 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
       __syncthreads();
       for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
         const int c = i & 3;
-        if (st.cg_active[c]) P[i] = R[i] + (T)st.beta_cg[c] * P[i];
+        if (st.cg_active[c]) P[i] = R[i] + scal[4 + c] * P[i];
       }
       __syncthreads();
     }
@@ -813,7 +858,7 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
       __syncthreads();
       const int nmax = st.n_max;
       for (int pass = 0; pass < 2 && nmax > 0; ++pass) {
-        gs_sweep<T>(U, SU, Lv, KV, SL, m, m_cap, nmax, true, st, coef, HS, nu);
+        gs_sweep<T>(U, SU, Lv, KV, SL, m, m_cap, nmax, true, st, coef, coefT, HS, nu);
         if (threadIdx.x < 4) {
           double s = 0;
           for (int mm = 0; mm < nmax; ++mm) s += coef[mm * 4 + threadIdx.x] * coef[mm * 4 + threadIdx.x];
@@ -824,7 +869,7 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
         for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
           const int r = i >> 2, c = i & 3;
           T v = Lv[i];
-          for (int mm = 0; mm < nmax; ++mm) v -= (T)coef[mm * 4 + c] * U[(size_t)mm * m_cap * 4 + 4 * r + c];
+          for (int mm = 0; mm < nmax; ++mm) v -= coefT[mm * 4 + c] * U[(size_t)mm * m_cap * 4 + 4 * r + c];
           Lv[i] = v;
         }
         __syncthreads();
@@ -843,6 +888,7 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
           if (beta > A.tau * beta_pre) {
             st.accept[c] = 1;
             st.beta_inv[c] = 1.0 / beta;
+            scal[8 + c] = (T)st.beta_inv[c];
           } else if (st.src[c] == SRC_S) {
             st.act[c] = ACT_LOAD_K;   // s_j already in the span: continue with H u_n
             st.src[c] = SRC_H;
@@ -861,7 +907,7 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
         for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
           const int r = i >> 2, c = i & 3;
           if (st.accept[c]) {
-            const T bi = (T)st.beta_inv[c];
+            const T bi = scal[8 + c];
             const T u = Lv[i] * bi;
             const T su = SL[i] * bi;
             const size_t o = (size_t)st.n[c] * m_cap * 4 + 4 * r + c;
@@ -915,7 +961,7 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
         st.n_max = nm;
       }
       __syncthreads();
-      gs_sweep<T>(U, SU, Lv, KV, SL, m, m_cap, st.n_max, false, st, coef, HS, nu);
+      gs_sweep<T>(U, SU, Lv, KV, SL, m, m_cap, st.n_max, false, st, coef, coefT, HS, nu);
     }
 
     // ---- 4./5. reduced problems (one warp per column) and outputs ----------------------
@@ -953,6 +999,15 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
         st.accept[c] = ok;    // reused as "reduced solve succeeded"
       }
     }
+    __syncthreads();
+    // C in the arithmetic type, once per column, into the (now free) L region
+    for (int i = threadIdx.x; i < 4 * nu * nu; i += blockDim.x) {
+      const int c = i / (nu * nu), n = (i / nu) % nu, a = i % nu;
+      if (!st.accept[c] || n >= st.n[c] || a >= st.n[c]) continue;
+      const double* Hm = RM + (size_t)c * rm_col;
+      T* CT = reinterpret_cast<T*>(const_cast<double*>(Hm) + (size_t)nu * ld);
+      CT[n * ld + a] = (T)Hm[n * ld + a];
+    }
     // ---- outputs of the four columns, all threads -----------------------------------------
     const int e0 = lrow[t0], e1 = lrow[t0 + 1];
     const int64_t rbase = A.row_ptr[atom];
@@ -971,9 +1026,10 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
       const double* Hm = RM + (size_t)c * rm_col;
       const RedScratch wsc(const_cast<double*>(Hm) + (size_t)2 * nu * ld, nu);
       const int jr = 4 * t0 + c;
+      const T* CT = reinterpret_cast<const T*>(Hm + (size_t)nu * ld);
       T vj = 0, svj = 0;
       for (int n = 0; n < nv; ++n) {
-        const T cn = (T)Hm[n * ld + a];
+        const T cn = CT[n * ld + a];
         vj += U[(size_t)n * m_cap * 4 + 4 * jr + c] * cn;
         svj += SU[(size_t)n * m_cap * 4 + 4 * jr + c] * cn;
       }
@@ -991,13 +1047,14 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
         const RedScratch wsc(const_cast<double*>(Hm) + (size_t)2 * nu * ld, nu);
         const int k = (int)(lblk[e] - rbase);
         const T* urow = U + 4 * (4 * (int)lcol[e] + r) + c;
+        const T* CT = reinterpret_cast<const T*>(Hm + (size_t)nu * ld);
         double* out = A.vp + ((A.blk_off[widx] + k) * 16 + c * 4 + r) * (int64_t)nu;
         for (int a0 = 0; a0 < nv; a0 += 8) {
           T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
           for (int n = 0; n < nv; ++n) {
             const T un = urow[(size_t)n * m_cap * 4];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[j] += un * (a0 + j < nv ? (T)Hm[n * ld + a0 + j] : (T)0);
+            for (int j = 0; j < 8; ++j) acc[j] += un * (a0 + j < nv ? CT[n * ld + a0 + j] : (T)0);
           }
 #pragma unroll
           for (int j = 0; j < 8; ++j)
@@ -1023,6 +1080,7 @@ __global__ void cluster_size_kernel(Args<double> A, int32_t* sizes) {
   for (int64_t i = wglobal; i < A.n_sel; i += wstride) {
     const int64_t a = A.sel[i];
     const double px = A.pos[3 * a], py = A.pos[3 * a + 1], pz = A.pos[3 * a + 2];
+    const float pxf = A.posf[3 * a], pyf = A.posf[3 * a + 1], pzf = A.posf[3 * a + 2];
     int rx[3], ry[3], rz[3];
     const int nx = cell_range(cell_coord(px, A.cell_len[0], A.ncell[0]), A.ncell[0], rx);
     const int ny = cell_range(cell_coord(py, A.cell_len[1], A.ncell[1]), A.ncell[1], ry);
@@ -1031,14 +1089,9 @@ __global__ void cluster_size_kernel(Args<double> A, int32_t* sizes) {
     for (int ci = 0; ci < nx * ny * nz; ++ci) {
       const int ix = ci / (ny * nz), iy = (ci / nz) % ny, iz = ci % nz;
       const int c = (rx[ix] * A.ncell[1] + ry[iy]) * A.ncell[2] + rz[iz];
-      for (int k = A.cell_start[c] + lane; k < A.cell_start[c + 1]; k += 32) {
-        const int b = A.cell_atoms[k];
-        const double dx = min_image(A.pos[3 * b] - px, A.box[0]);
-        const double dy = min_image(A.pos[3 * b + 1] - py, A.box[1]);
-        const double dz = min_image(A.pos[3 * b + 2] - pz, A.box[2]);
-        const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        count += r2 <= A.R2;
-      }
+      for (int k = A.cell_start[c] + lane; k < A.cell_start[c + 1]; k += 32)
+        count += within_R(A.pos, A.posf, A.box, A.R2, A.pre_lo, A.pre_hi, A.cell_atoms[k], px, py, pz, pxf, pyf,
+                          pzf);
     }
     count = warp_sum(count);
     if (lane == 0) sizes[i] = count;
@@ -1053,12 +1106,17 @@ void fill_system_args(Args<TV>& A, const mka_system* s) {
   A.valH = reinterpret_cast<const TV*>(s->d_valH);
   A.valS = reinterpret_cast<const TV*>(s->d_valS);
   A.pos = s->d_pos;
+  A.posf = s->d_posf;
   for (int d = 0; d < 3; ++d) {
     A.box[d] = s->box[d];
     A.ncell[d] = s->cells.n[d];
     A.cell_len[d] = s->cells.len[d];
   }
   A.R2 = s->R * s->R;
+  const double lmax = std::max(s->box[0], std::max(s->box[1], s->box[2]));
+  const double margin = std::max(1e-3, 1e-5 * lmax / s->R);
+  A.pre_lo = (float)(1.0 - margin);
+  A.pre_hi = (float)(1.0 + margin);
   A.cell_start = s->cells.start;
   A.cell_atoms = s->cells.atoms;
 }

@@ -226,20 +226,18 @@ __global__ void sum_kernel(const double* x, int64_t n, double* out) {
   }
 }
 
-__global__ void count_kernel(const double* eps, const double* w, int64_t n, double mu_host, const double* mu_dev,
-                             double kT, double* out) {
-  __shared__ double part[kRedThreads];
+// 2 sum f(eps; mu) w: per-block partial sums (fixed grid), added in order by sum_kernel.
+__global__ void count_partial_kernel(const double* eps, const double* w, int64_t n, double mu_host, const double* mu_dev,
+                                     double kT, double* partial) {
+  __shared__ double red[kRedThreads / 32];
   const double mu = mu_dev ? *mu_dev : mu_host;
-  double s = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x)
-    if (w[i] != 0.0) s += fermi(eps[i], mu, kT) * w[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < (int)blockDim.x; ++k) t += part[k];
-    *out = 2.0 * t;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double wi = w[i];
+    if (wi != 0.0) acc += fermi(eps[i], mu, kT) * wi;
   }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = 2.0 * s;
 }
 
 // ---- global BSR SpMV: one warp per block row, 16-byte vector loads of the values ----
@@ -374,8 +372,9 @@ mka_status density_enqueue(const mka_system* sys, const int64_t* sel, const int6
   density_kernel<<<(unsigned)n_sel, 128, 0, st>>>(vp, eps, blk_off, self_k, sel, sys->d_row_ptr, sys->d_valH,
                                                   sys->storage, nu, 0.0, mu_dev, kT, rho_out, tmp);
   sum_kernel<<<1, kRedThreads, 0, st>>>(tmp, n_sel, tmp + n_sel);
-  count_kernel<<<1, kRedThreads, 0, st>>>(eps, w, 4 * n_sel * nu, 0.0, mu_dev, kT, tmp + n_sel + 1);
-  count_launches(3);
+  count_partial_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(eps, w, 4 * n_sel * nu, 0.0, mu_dev, kT, tmp + n_sel + 2);
+  sum_kernel<<<1, kRedThreads, 0, st>>>(tmp + n_sel + 2, kRedBlocks, tmp + n_sel + 1);
+  count_launches(4);
   MKA_CUDA_TRY(cudaGetLastError());
   return MKA_OK;
 }
@@ -419,14 +418,15 @@ mka_status launch_density(mka_system* sys, mka_result* res, double mu, double kT
                           double* n_elec) {
   cudaStream_t st = res->stream;
   double* tmp = nullptr;
-  MKA_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(double) * (res->n_sel + 2), st));
+  MKA_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(double) * (res->n_sel + 2 + kRedBlocks), st));
   density_kernel<<<(unsigned)res->n_sel, 128, 0, st>>>(res->d_vp, res->d_eps, res->d_blk_off, res->d_self,
                                                        res->d_sel, sys->d_row_ptr, sys->d_valH, sys->storage,
                                                        res->nu, mu, nullptr, kT, rho_out, tmp);
   sum_kernel<<<1, kRedThreads, 0, st>>>(tmp, res->n_sel, tmp + res->n_sel);
-  count_kernel<<<1, kRedThreads, 0, st>>>(res->d_eps, res->d_w, res->n_cols * res->nu, mu, nullptr, kT,
-                                          tmp + res->n_sel + 1);
-  count_launches(3);
+  count_partial_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(res->d_eps, res->d_w, res->n_cols * res->nu, mu, nullptr,
+                                                           kT, tmp + res->n_sel + 2);
+  sum_kernel<<<1, kRedThreads, 0, st>>>(tmp + res->n_sel + 2, kRedBlocks, tmp + res->n_sel + 1);
+  count_launches(4);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && (e_band || n_elec)) {
     double h[2];

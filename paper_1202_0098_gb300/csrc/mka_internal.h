@@ -47,6 +47,8 @@ struct mka_system {
   void* d_valH = nullptr;       // storage-typed [nnzb][16]
   void* d_valS = nullptr;
   double* d_pos = nullptr;      // [n_atoms][3], wrapped into the box
+  float* d_posf = nullptr;      // the same rounded to FP32 (distance prefilter)
+  int max_cluster = -1;         // largest cluster over all atoms (-1: not computed yet)
   mka::CellList cells{};
   // host copies of the pattern
   std::vector<int32_t> h_row_ptr, h_col;
@@ -133,6 +135,8 @@ mka_status find_mu_enqueue(const double* eps, const double* w, int64_t n, double
 mka_status density_enqueue(const mka_system* sys, const int64_t* sel, const int64_t* blk_off, const int32_t* self_k,
                            const double* vp, const double* eps, const double* w, int64_t n_sel, int nu,
                            const double* mu_dev, double kT, double* rho_out, double* tmp, cudaStream_t st);
+// tmp of density_enqueue holds n_sel + 2 + kDensityTmpExtra doubles.
+constexpr int kDensityTmpExtra = 608;
 
 size_t storage_bytes(int storage);
 

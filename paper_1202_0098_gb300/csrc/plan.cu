@@ -87,6 +87,7 @@ struct mka_plan {
   int64_t* h_stage = nullptr;      // pinned: atoms [max_atoms], block offsets [max_atoms + 1]
   cudaEvent_t staged = nullptr;
   cudaStream_t capture = nullptr;  // private stream the graphs are captured on (never executes work)
+  cudaEvent_t k0 = nullptr, k1 = nullptr;   // recorded around the per-atom kernel inside every graph
   std::vector<mka::GraphEntry> graphs;
 };
 
@@ -121,10 +122,12 @@ mka_status plan_alloc(mka_plan* P) {
   MKA_CUDA_TRY(cudaMalloc(&P->sizes, sizeof(int32_t) * A));
   MKA_CUDA_TRY(cudaMalloc(&P->bins, sizeof(int32_t) * kSizeBins));
   MKA_CUDA_TRY(cudaMalloc(&P->mu_buf, mu_buffer_bytes()));
-  MKA_CUDA_TRY(cudaMalloc(&P->dev_out, sizeof(double) * (A + 4)));
+  MKA_CUDA_TRY(cudaMalloc(&P->dev_out, sizeof(double) * (A + 4 + 1024)));   // mu, partials, E, N, count partials
   MKA_CUDA_TRY(cudaMallocHost(&P->h_stage, sizeof(int64_t) * (2 * A + 1)));
   MKA_CUDA_TRY(cudaEventCreateWithFlags(&P->staged, cudaEventDisableTiming));
   MKA_CUDA_TRY(cudaStreamCreateWithFlags(&P->capture, cudaStreamNonBlocking));
+  MKA_CUDA_TRY(cudaEventCreate(&P->k0));
+  MKA_CUDA_TRY(cudaEventCreate(&P->k1));
   return MKA_OK;
 }
 
@@ -169,8 +172,10 @@ mka_status plan_enqueue(mka_plan* P, int64_t n, double n_electrons, double kT, d
   a.scratch = P->scratch;
   a.counter = P->counter;
   a.grid = (int)std::min<int64_t>(n, P->grid);
+  MKA_CUDA_TRY(cudaEventRecordWithFlags(P->k0, st, cudaEventRecordExternal));
   mka_status s = atoms_launch(P->sys, P->prm.arith, P->cf, a, st);
   if (s) return s;
+  MKA_CUDA_TRY(cudaEventRecordWithFlags(P->k1, st, cudaEventRecordExternal));
   const int nu = r->nu;
   s = find_mu_enqueue(r->d_eps, r->d_w, 4 * n * nu, n_electrons, kT, 1e-12, kHalvings, P->mu_buf, P->dev_out, st);
   if (s) return s;
@@ -187,6 +192,8 @@ void mka_plan_destroy(mka_plan* P) {
   for (auto& g : P->graphs) cudaGraphExecDestroy(g.exec);
   if (P->staged) cudaEventDestroy(P->staged);
   if (P->capture) cudaStreamDestroy(P->capture);
+  if (P->k0) cudaEventDestroy(P->k0);
+  if (P->k1) cudaEventDestroy(P->k1);
   cudaFreeHost(P->h_stage);
   cudaFree(P->scratch);
   cudaFree(P->counter);
@@ -222,14 +229,18 @@ mka_status mka_plan_create(mka_system* sys, int64_t max_atoms, const mka_solve_p
   P->prm = *prm;
   P->tune = t;
   P->max_atoms = max_atoms;
-  // largest cluster of the whole system sizes every work slot
-  std::vector<int32_t> sz(sys->n_atoms);
-  mka_status s = mka_cluster_sizes(sys, nullptr, sys->n_atoms, sz.data());
-  if (s) {
-    delete P;
-    return s;
+  // largest cluster of the whole system sizes every work slot (computed once per system)
+  if (sys->max_cluster < 0) {
+    std::vector<int32_t> sz(sys->n_atoms);
+    mka_status s0 = mka_cluster_sizes(sys, nullptr, sys->n_atoms, sz.data());
+    if (s0) {
+      delete P;
+      return s0;
+    }
+    sys->max_cluster = *std::max_element(sz.begin(), sz.end());
   }
-  P->max_cl = *std::max_element(sz.begin(), sz.end());
+  mka_status s = MKA_OK;
+  P->max_cl = sys->max_cluster;
   if (P->max_cl > MKA_MAX_CLUSTER_ATOMS) {
     delete P;
     return fail(MKA_ERR_CLUSTER_TOO_LARGE, "a cluster of the system exceeds MKA_MAX_CLUSTER_ATOMS");
@@ -315,6 +326,13 @@ mka_status mka_plan_scalars(mka_plan* P, double* mu, double* e_band, double* n_e
   if (mu) *mu = h[0];
   if (e_band) *e_band = h[1];
   if (n_elec) *n_elec = h[2];
+  return MKA_OK;
+}
+
+mka_status mka_plan_kernel_ms(mka_plan* P, float* ms) {
+  if (!P || !ms) return fail(MKA_ERR_INVALID_ARG, "plan and ms are required");
+  MKA_CUDA_TRY(cudaEventSynchronize(P->k1));
+  MKA_CUDA_TRY(cudaEventElapsedTime(ms, P->k0, P->k1));
   return MKA_OK;
 }
 

@@ -188,6 +188,11 @@ mka_status upload_common(mka_system* s, const std::vector<double>& wpos, bool co
   int64_t N = s->n_atoms;
   MKA_CUDA_TRY(cudaMalloc(&s->d_pos, sizeof(double) * 3 * N));
   MKA_CUDA_TRY(cudaMemcpy(s->d_pos, wpos.data(), sizeof(double) * 3 * N, cudaMemcpyHostToDevice));
+  {
+    std::vector<float> pf(wpos.begin(), wpos.end());
+    MKA_CUDA_TRY(cudaMalloc(&s->d_posf, sizeof(float) * 3 * N));
+    MKA_CUDA_TRY(cudaMemcpy(s->d_posf, pf.data(), sizeof(float) * 3 * N, cudaMemcpyHostToDevice));
+  }
   MKA_CUDA_TRY(cudaMalloc(&s->d_row_ptr, sizeof(int32_t) * (N + 1)));
   MKA_CUDA_TRY(cudaMemcpy(s->d_row_ptr, s->h_row_ptr.data(), sizeof(int32_t) * (N + 1), cudaMemcpyHostToDevice));
   MKA_CUDA_TRY(cudaMalloc(&s->d_col, sizeof(int32_t) * std::max<int64_t>(s->nnzb, 1)));
@@ -244,6 +249,7 @@ void mka_system_destroy(mka_system* s) {
   cudaFree(s->d_valH);
   cudaFree(s->d_valS);
   cudaFree(s->d_pos);
+  cudaFree(s->d_posf);
   cudaFree(s->cells.start);
   cudaFree(s->cells.atoms);
   delete s;

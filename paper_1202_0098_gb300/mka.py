@@ -29,7 +29,7 @@ EXPORTED = [
     "mka_build_system", "mka_build_system_bsr", "mka_system_info", "mka_system_copy_bsr", "mka_cluster_sizes",
     "mka_system_destroy", "mka_spmv", "mka_solve_columns", "mka_solve_columns_static", "mka_result_info", "mka_result_copy_levels",
     "mka_result_device_levels", "mka_result_destroy", "mka_find_mu", "mka_density_energy", "mka_greens",
-    "mka_plan_create", "mka_plan_run", "mka_plan_scalars", "mka_plan_result", "mka_plan_info", "mka_plan_destroy",
+    "mka_plan_create", "mka_plan_run", "mka_plan_scalars", "mka_plan_kernel_ms", "mka_plan_result", "mka_plan_info", "mka_plan_destroy",
     "mka_autotune", "mka_kernel_launches", "mka_last_error", "mka_status_string",
 ]
 
@@ -90,6 +90,7 @@ def load(path: str | None = None) -> C.CDLL:
         "mka_plan_run": [P, P, I64, D, D, P],
         "mka_plan_scalars": [P, P, P, P],
         "mka_plan_result": [P, P],
+        "mka_plan_kernel_ms": [P, P],
         "mka_plan_info": [P, P, P, P],
         "mka_autotune": [P, P, P, I64, D, D, C.c_char_p, P, P],
     }
@@ -301,6 +302,12 @@ def mka_plan_scalars(plan) -> tuple[float, float, float]:
     mu, e, n = C.c_double(), C.c_double(), C.c_double()
     _check(load().mka_plan_scalars(plan, C.byref(mu), C.byref(e), C.byref(n)), "mka_plan_scalars")
     return mu.value, e.value, n.value
+
+
+def mka_plan_kernel_ms(plan) -> float:
+    ms = C.c_float()
+    _check(load().mka_plan_kernel_ms(plan, C.byref(ms)), "mka_plan_kernel_ms")
+    return ms.value
 
 
 def mka_plan_result(plan) -> C.c_void_p:
