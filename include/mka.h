@@ -244,6 +244,55 @@ mka_status mka_density_energy(mka_system* sys, mka_result* res, double mu, doubl
  * [n_blocks][4][4][2]. Needs keep_vectors = 1. */
 mka_status mka_greens(mka_system* sys, mka_result* res, double z_re, double z_im, double* g_out);
 
+/* ---- learned warm start for the inner CG ---------------------------------- */
+/* The inner CG for s_j = S^{-1} e_j (Sec. 2) may start from any x0. A small
+ * network predicts x0 on the 17-atom patch around j's atom (the atom and its 16
+ * nearest neighbours by minimum-image distance, ties by atom id; 4 orbitals
+ * each = 68 values, patch order then s, px, py, pz). Its 132 inputs per column:
+ * the 32 nearest neighbours within 3 A as (d, l, m, n), (l, m, n) the direction
+ * cosines of r_b - r_a, zeros beyond, then a one-hot of the column's orbital.
+ * Network 132 -> 128 -> 128 -> 68, SiLU after the hidden layers; parameters
+ * packed W1 [128][132], b1, W2 [128][128], b2, W3 [68][128], b3 (FP32 master,
+ * BF16 for every product, FP32 sums); loss = mean squared error over the batch
+ * and the 68 outputs; Adam (beta 0.9 / 0.999, eps 1e-8, bias-corrected).
+ * CG from the prediction always runs to the solve's tolerance; where the
+ * prediction's residual is no smaller than ||e_j|| the column starts from zero
+ * instead (counted as a fallback). */
+typedef struct mka_mlp mka_mlp;
+
+int64_t mka_mlp_num_params(void);
+/* New network, He-uniform weights and zero biases from a seeded generator. */
+mka_status mka_mlp_create(uint64_t seed, mka_mlp** out);
+void mka_mlp_destroy(mka_mlp* net);
+/* Host FP32 parameters in the packed order (set resets the Adam state). get with
+ * bf16_rounded = 1 returns the BF16 values the products use. */
+mka_status mka_mlp_set_params(mka_mlp* net, const float* params);
+mka_status mka_mlp_get_params(const mka_mlp* net, float* params, int bf16_rounded);
+/* Y = net(X): device X [B][132], device Y [B][68], FP32. */
+mka_status mka_mlp_forward(mka_mlp* net, const float* X, float* Y, int64_t B, void* stream);
+/* Loss and its gradient with respect to the (BF16) parameters for device X, targets T
+ * [B][68]: grad (device, num_params floats) and loss (device, 1 float); either may be NULL. */
+mka_status mka_mlp_gradients(mka_mlp* net, const float* X, const float* T, int64_t B, float* grad,
+                             float* loss, void* stream);
+/* One Adam step on the batch (gradient as above); loss before the step into device `loss`
+ * (may be NULL). */
+mka_status mka_mlp_train_step(mka_mlp* net, const float* X, const float* T, int64_t B, float lr,
+                              float* loss, void* stream);
+/* Inputs of the 4 columns of each of n atoms (host list): device X [4n][132] and the
+ * patch atoms, device int32 [n][17] (-1 where fewer atoms lie within min(5.5 A, cell edge)). */
+mka_status mka_warm_start_features(const mka_system* sys, const int64_t* atoms, int64_t n, float* X,
+                                   int32_t* patch, void* stream);
+/* Training targets: the inner CG alone (x0 = 0, `arith`, tolerance cg_tol) for the 4
+ * columns of each atom, s_j written on the given patch: device Y [4n][68] (FP32), device
+ * iterations [4n] (may be NULL). */
+mka_status mka_cg_patch_targets(mka_system* sys, const int64_t* atoms, int64_t n, int arith, double cg_tol,
+                                const int32_t* patch, float* Y, int32_t* iters, void* stream);
+/* Network used by solves with use_warm_start = 1 (NULL detaches; not owned). */
+mka_status mka_system_set_warm_start(mka_system* sys, mka_mlp* net);
+/* Per-column warm-start fallback flags (1 = started from zero) of a solve made with
+ * use_warm_start = 1, into host int32 [n_cols]. */
+mka_status mka_result_copy_warm_start(const mka_result* res, int32_t* fallback);
+
 /* ---- persistent, graph-captured batches ---------------------------------- */
 
 /* Launch shape of the per-atom kernel. */
@@ -278,6 +327,10 @@ mka_status mka_plan_run(mka_plan* plan, const int64_t* atoms, int64_t n_sel, dou
 /* mu, band energy 2 sum_j sum_i rho_ij H_ji and electron count 2 sum f w of the
  * last batch (host outputs, any may be NULL); synchronises the plan's stream. */
 mka_status mka_plan_scalars(mka_plan* plan, double* mu, double* e_band, double* n_elec);
+
+/* Device time (ms) of the per-atom kernel in the last batch, from events the
+ * graph records around it; waits for that batch's kernel to finish. */
+mka_status mka_plan_kernel_ms(mka_plan* plan, float* ms);
 
 /* The plan's result object (levels, weights, status and kept rows of the last
  * batch), borrowed: valid until the next run or mka_plan_destroy, never

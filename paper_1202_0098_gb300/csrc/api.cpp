@@ -62,6 +62,7 @@ void mka_result_destroy(mka_result* r) {
   cudaFree(r->d_vp);
   cudaFree(r->d_self);
   cudaFree(r->d_mu_state);
+  cudaFree(r->d_fallback);
   delete r;
 }
 
@@ -75,7 +76,8 @@ mka_status mka_solve_columns(mka_system* sys, const int64_t* atoms, int64_t n_se
   if (prm->arith != MKA_FP64 && prm->arith != MKA_MIXED_FP32)
     return fail(MKA_ERR_INVALID_ARG, "arith must be MKA_FP64 or MKA_MIXED_FP32");
   if (!(prm->cg_tol > 0) || prm->cg_maxit < 1) return fail(MKA_ERR_INVALID_ARG, "need cg_tol > 0, cg_maxit >= 1");
-  if (prm->use_warm_start) return fail(MKA_ERR_INVALID_ARG, "warm start needs a loaded network (none loaded)");
+  if (prm->use_warm_start && !sys->warm)
+    return fail(MKA_ERR_INVALID_ARG, "use_warm_start needs a network attached with mka_system_set_warm_start");
   cudaStream_t st = (cudaStream_t)stream;
   mka_result* r = new mka_result();
   r->sys = sys;
@@ -111,6 +113,7 @@ mka_status mka_solve_columns(mka_system* sys, const int64_t* atoms, int64_t n_se
   ALLOC(r->d_cg_iters, sizeof(int32_t) * nc);
   ALLOC(r->d_status, sizeof(int32_t) * nc);
   ALLOC(r->d_self, sizeof(int32_t) * r->n_sel);
+  if (prm->use_warm_start) ALLOC(r->d_fallback, sizeof(int32_t) * nc);
   if (r->keep) ALLOC(r->d_vp, sizeof(double) * r->n_blocks * 16 * nu);
 #undef ALLOC
   if (e == cudaSuccess)
@@ -171,6 +174,75 @@ mka_status mka_result_copy_levels(const mka_result* r, double* eps, double* w, i
       return fail((mka_status)v, "column " + std::to_string(c) + ": " + mka_status_string((mka_status)v));
     }
   }
+  return MKA_OK;
+}
+
+mka_status mka_result_copy_warm_start(const mka_result* r, int32_t* fallback) {
+  if (!r || !fallback) return fail(MKA_ERR_INVALID_ARG, "result and fallback are required");
+  if (!r->d_fallback) return fail(MKA_ERR_INVALID_ARG, "the result was solved without the learned warm start");
+  MKA_CUDA_TRY(cudaStreamSynchronize(r->stream));
+  MKA_CUDA_TRY(cudaMemcpy(fallback, r->d_fallback, sizeof(int32_t) * r->n_cols, cudaMemcpyDeviceToHost));
+  return MKA_OK;
+}
+
+mka_status mka_cg_patch_targets(mka_system* sys, const int64_t* atoms, int64_t n, int arith, double cg_tol,
+                                const int32_t* patch, float* Y, int32_t* iters, void* stream) {
+  if (!sys || !atoms || n < 1 || !patch || !Y) return fail(MKA_ERR_INVALID_ARG, "bad target arguments");
+  if (arith != MKA_FP64 && arith != MKA_MIXED_FP32) return fail(MKA_ERR_INVALID_ARG, "arith must be FP64 or FP32");
+  if (!(cg_tol > 0)) return fail(MKA_ERR_INVALID_ARG, "need cg_tol > 0");
+  std::vector<int64_t> sel(atoms, atoms + n);
+  for (int64_t v : sel)
+    if (v < 0 || v >= sys->n_atoms) return fail(MKA_ERR_INVALID_ARG, "atom index out of range");
+  std::vector<int32_t> sizes(n);
+  mka_status s = mka_cluster_sizes(sys, atoms, n, sizes.data());
+  if (s) return s;
+  const int max_cl = *std::max_element(sizes.begin(), sizes.end());
+  if (max_cl > MKA_MAX_CLUSTER_ATOMS) return fail(MKA_ERR_CLUSTER_TOO_LARGE, "cluster larger than the cap");
+  AtomsConfig cf{};
+  s = atoms_config(sys, 1, arith, max_cl, 256, 0, &cf);     // basis unused: smallest subspace
+  if (s) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t grid = std::min<int64_t>(n, cf.grid_max);
+  char* buf = nullptr;
+  const size_t scratch_bytes = cf.slot_bytes * grid + 256;
+  const size_t extra = sizeof(int64_t) * n + sizeof(int32_t) * 8 * n + 256;
+  MKA_CUDA_TRY(cudaMallocAsync(&buf, scratch_bytes + extra, st));
+  int64_t* d_sel = reinterpret_cast<int64_t*>(buf + scratch_bytes);
+  int32_t* d_status = reinterpret_cast<int32_t*>(d_sel + n);
+  int32_t* d_iters = d_status + 4 * n;
+  int* counter = reinterpret_cast<int*>(d_iters + 4 * n);
+  cudaError_t e = cudaMemcpyAsync(d_sel, sel.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(buf, st);
+    return cuda_fail(e, "mka_cg_patch_targets");
+  }
+  AtomsLaunchArgs a{};
+  a.sel = d_sel;
+  a.n_sel = n;
+  a.p = 1;
+  a.q = 0;
+  a.cg_tol = cg_tol;
+  a.cg_maxit = 1000;
+  a.status = d_status;
+  a.cg_iters = iters ? iters : d_iters;
+  a.scratch = buf;
+  a.counter = counter;
+  a.grid = (int)grid;
+  a.patch = patch;
+  a.cg_only = 1;
+  a.cg_target = Y;
+  s = atoms_launch(sys, arith, cf, a, st);
+  std::vector<int32_t> stv(4 * n);
+  if (s == MKA_OK) {
+    e = cudaMemcpyAsync(stv.data(), d_status, sizeof(int32_t) * 4 * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaFreeAsync(buf, st);
+  if (s) return s;
+  if (e != cudaSuccess) return cuda_fail(e, "mka_cg_patch_targets");
+  for (int64_t i = 0; i < 4 * n; ++i)
+    if (stv[i] != MKA_OK) return fail((mka_status)stv[i], "inner CG failed for column " + std::to_string(i));
   return MKA_OK;
 }
 

@@ -124,6 +124,13 @@ struct Args {
   double* vp;
   const int64_t* blk_off;
   int32_t* self_k;
+  // learned warm start: predicted s_j on the 17-atom patch, or NULL for x0 = 0
+  const float* x0;          // [4 n_sel][68]
+  const int32_t* patch;     // [n_sel][17] atom ids (-1: none)
+  int32_t* fallback;        // [4 n_sel]: 1 where the prediction was no better than x0 = 0 (may be NULL)
+  // CG-only mode: stop after the inner CG and write s_j on the patch (training targets)
+  int cg_only;
+  float* cg_target;         // [4 n_sel][68]
 };
 
 // ---- small CTA helpers -------------------------------------------------------------
@@ -313,6 +320,45 @@ __device__ __forceinline__ void spmm4(const TV* __restrict__ val, const int* lro
   __syncthreads();
 }
 
+// r = e_j - A x for the four columns in FP32 with error-free products (FMA TwoProd) and
+// compensated sums (Knuth's TwoSum), so that the residual is accurate to a few rounding
+// errors of its own size rather than of |A| |x|. Explicit _rn operations keep the compiler
+// from contracting them.
+template <typename TV>
+__device__ void resid4_comp(const TV* __restrict__ val, const int* lrow, const uint16_t* lcol, const int* lblk,
+                            int ncl, const float* __restrict__ x, float* __restrict__ r, int jrow0) {
+  for (int row = threadIdx.x; row < 4 * ncl; row += blockDim.x) {
+    const int t = row >> 2, i = row & 3;
+    float hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+    for (int e = lrow[t]; e < lrow[t + 1]; ++e) {
+      float v[4];
+      RowLoad<TV, float>::load(val, lblk[e], i, v);
+      const float* xb = x + (size_t)lcol[e] * 16;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float xk[4];
+        ld4(xb + 4 * k, xk);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float p = __fmul_rn(v[k], xk[q]);
+          const float pe = fmaf(v[k], xk[q], -p);
+          const float s = __fadd_rn(hi[q], p);
+          const float bb = __fsub_rn(s, hi[q]);
+          const float err = __fadd_rn(__fsub_rn(hi[q], __fsub_rn(s, bb)), __fsub_rn(p, bb));
+          hi[q] = s;
+          lo[q] = __fadd_rn(lo[q], __fadd_rn(err, pe));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float e = (row == jrow0 + q) ? 1.0f : 0.0f;
+      r[4 * row + q] = __fsub_rn(__fsub_rn(e, hi[q]), lo[q]);
+    }
+  }
+  __syncthreads();
+}
+
 // Per-column dot products over the cluster rows: per-thread partial sums in T
 // (a few terms each), combined across threads in FP64.
 template <typename T>
@@ -330,7 +376,7 @@ __device__ __forceinline__ void dot4(const T* a, const T* b, int m, double* red,
 struct AtomState {
   int n[4], src[4], seam_done[4], active[4], accept[4], act[4], next_s[4], proj[4];
   int it[4], cg_active[4], status[4];
-  double beta_inv[4], csum[4], rr[4], alpha[4], beta_cg[4];
+  double beta_inv[4], csum[4], rr[4], alpha[4], beta_cg[4], cg_stop[4];
   int ncl, t0, flag, n_max, proj_any, acc_mask, act_mask;
 };
 
@@ -760,71 +806,167 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
     }
     const int m = 4 * ncl;
     const int t0 = st.t0;
-    // ---- 2. inner CG: S s = e_j, x0 = 0 ----------------------------------------------
+    // ---- 2. inner CG: S s = e_j from x0 = 0 or the learned patch values ----------------
     T* P = V0;
     T* AP = V1;
     T* R = V2;
     for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
-      const int r = i >> 2, c = i & 3;
-      const T e = (r == 4 * t0 + c) ? (T)1 : (T)0;
       SJ[i] = 0;
-      R[i] = e;
-      P[i] = e;
+      P[i] = 0;
     }
     if (threadIdx.x < 4) {
       const int c = threadIdx.x;
       st.rr[c] = 1.0;
       st.it[c] = 0;
       st.status[c] = ST_OK;
-      st.cg_active[c] = !(1.0 <= A.cg_tol);
+      st.act[c] = 0;    // reused: warm-start fallback flag
     }
     __syncthreads();
-    for (int it = 0; it < A.cg_maxit; ++it) {
-      const int cmask = st.cg_active[0] | (st.cg_active[1] << 1) | (st.cg_active[2] << 2) | (st.cg_active[3] << 3);
-      if (!cmask) break;
-      spmm4<TV, T>(A.valS, lrow, lcol, lblk, ncl, P, AP, cmask);
-      dot4<T>(P, AP, m, red, sums);
-      if (threadIdx.x < 4) {
-        const int c = threadIdx.x;
-        double a = 0.0;
-        if (st.cg_active[c]) {
-          if (!(sums[c] > 0.0)) {
-            st.status[c] = ST_NOT_SPD;
-            st.cg_active[c] = 0;
-          } else {
-            a = st.rr[c] / sums[c];
-          }
-        }
-        st.alpha[c] = a;
-        scal[c] = (T)a;
+    if (A.x0) {
+      for (int i = threadIdx.x; i < 4 * 68; i += blockDim.x) {   // (column, patch atom, orbital)
+        const int c = i / 68, rem = i % 68, k = rem >> 2, o = rem & 3;
+        const int pa = A.patch[widx * 17 + k];
+        const int lk = pa >= 0 ? find_local(cl, ncl, pa) : -1;
+        if (lk < 0) continue;
+        const T v = (T)A.x0[(4 * widx + c) * 68 + rem];
+        SJ[4 * (4 * lk + o) + c] = v;
+        P[4 * (4 * lk + o) + c] = v;
       }
       __syncthreads();
+      spmm4<TV, T>(A.valS, lrow, lcol, lblk, ncl, P, AP, 15);
       for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
-        const int c = i & 3;
-        if (st.cg_active[c]) {
-          const T a = scal[c];
-          SJ[i] += a * P[i];
-          R[i] -= a * AP[i];
-        }
+        const int r = i >> 2, c = i & 3;
+        R[i] = ((r == 4 * t0 + c) ? (T)1 : (T)0) - AP[i];
       }
       __syncthreads();
       dot4<T>(R, R, m, red, sums);
       if (threadIdx.x < 4) {
         const int c = threadIdx.x;
-        if (st.cg_active[c]) {
-          st.beta_cg[c] = sums[c] / st.rr[c];
-          scal[4 + c] = (T)st.beta_cg[c];
+        if (!(sums[c] < 1.0)) {
+          st.act[c] = 1;         // no better than x0 = 0: start from zero
+        } else {
           st.rr[c] = sums[c];
-          st.it[c] += 1;
-          if (sqrt(sums[c]) <= A.cg_tol) st.cg_active[c] = 0;
         }
       }
       __syncthreads();
       for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
-        const int c = i & 3;
-        if (st.cg_active[c]) P[i] = R[i] + scal[4 + c] * P[i];
+        const int r = i >> 2, c = i & 3;
+        if (st.act[c]) {
+          SJ[i] = 0;
+          R[i] = (r == 4 * t0 + c) ? (T)1 : (T)0;
+        }
+        P[i] = R[i];
+      }
+    } else {
+      for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
+        const int r = i >> 2, c = i & 3;
+        const T e = (r == 4 * t0 + c) ? (T)1 : (T)0;
+        R[i] = e;
+        P[i] = e;
+      }
+    }
+    if (threadIdx.x < 4) {
+      st.cg_stop[threadIdx.x] = A.cg_tol;
+      st.cg_active[threadIdx.x] = sqrt(st.rr[threadIdx.x]) > A.cg_tol;
+    }
+    __syncthreads();
+    // Phase 0: CG to the tolerance. Phase 1 (FP32 arithmetic only): the true residual of x,
+    // recomputed with error-free products and compensated sums, replaces the recursive one and
+    // CG continues until it has dropped 30-fold, which takes x to FP32 rounding accuracy (the
+    // seam vector s_j lies mostly inside K_p(H; e_j), so its error would otherwise be magnified).
+    constexpr int kPhases = sizeof(T) == 4 ? 2 : 1;
+    for (int phase = 0; phase < kPhases; ++phase) {
+      int maxit = A.cg_maxit;
+      if (phase == 1) {
+        maxit = 20;
+        for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) P[i] = SJ[i];
+        __syncthreads();
+        if constexpr (sizeof(T) == 4)
+          resid4_comp<TV>(A.valS, lrow, lcol, lblk, ncl, reinterpret_cast<const float*>(P),
+                          reinterpret_cast<float*>(R), 4 * t0);
+        dot4<T>(R, R, m, red, sums);
+        if (threadIdx.x < 4) {
+          const int c = threadIdx.x;
+          st.rr[c] = sums[c];
+          st.cg_stop[c] = 3e-2 * sqrt(sums[c]);
+          st.cg_active[c] = (st.status[c] == ST_OK) && sums[c] > 0.0;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) P[i] = R[i];
+        __syncthreads();
+      }
+      for (int it = 0; it < maxit; ++it) {
+        const int cmask = st.cg_active[0] | (st.cg_active[1] << 1) | (st.cg_active[2] << 2) | (st.cg_active[3] << 3);
+        if (!cmask) break;
+        spmm4<TV, T>(A.valS, lrow, lcol, lblk, ncl, P, AP, cmask);
+        dot4<T>(P, AP, m, red, sums);
+        if (threadIdx.x < 4) {
+          const int c = threadIdx.x;
+          double a = 0.0;
+          if (st.cg_active[c]) {
+            if (!(sums[c] > 0.0)) {
+              st.status[c] = ST_NOT_SPD;
+              st.cg_active[c] = 0;
+            } else {
+              a = st.rr[c] / sums[c];
+            }
+          }
+          st.alpha[c] = a;
+          scal[c] = (T)a;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
+          const int c = i & 3;
+          if (st.cg_active[c]) {
+            const T a = scal[c];
+            SJ[i] += a * P[i];
+            R[i] -= a * AP[i];
+          }
+        }
+        __syncthreads();
+        dot4<T>(R, R, m, red, sums);
+        if (threadIdx.x < 4) {
+          const int c = threadIdx.x;
+          if (st.cg_active[c]) {
+            st.beta_cg[c] = sums[c] / st.rr[c];
+            scal[4 + c] = (T)st.beta_cg[c];
+            st.rr[c] = sums[c];
+            st.it[c] += 1;
+            if (sqrt(sums[c]) <= st.cg_stop[c]) st.cg_active[c] = 0;
+          }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
+          const int c = i & 3;
+          if (st.cg_active[c]) P[i] = R[i] + scal[4 + c] * P[i];
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x < 4) {
+        const int c = threadIdx.x;
+        // a column still running after the main phase did not converge; the refinement cap is no failure
+        if (phase == 0 && st.cg_active[c] && st.status[c] == ST_OK) st.status[c] = ST_NOCONV;
+        st.cg_active[c] = 0;
       }
       __syncthreads();
+    }
+    if (A.fallback && threadIdx.x < 4) A.fallback[4 * widx + threadIdx.x] = st.act[threadIdx.x];
+    if (A.cg_only) {
+      for (int i = threadIdx.x; i < 4 * 68; i += blockDim.x) {
+        const int c = i / 68, rem = i % 68, k = rem >> 2, o = rem & 3;
+        const int pa = A.patch[widx * 17 + k];
+        const int lk = pa >= 0 ? find_local(cl, ncl, pa) : -1;
+        A.cg_target[(4 * widx + c) * 68 + rem] = lk >= 0 ? (float)SJ[4 * (4 * lk + o) + c] : 0.0f;
+      }
+      if (threadIdx.x < 4) {
+        const int c = threadIdx.x;
+        int s = st.status[c];
+        if (st.cg_active[c] && s == ST_OK) s = ST_NOCONV;
+        A.status[4 * widx + c] = s;
+        A.cg_iters[4 * widx + c] = st.it[c];
+      }
+      __syncthreads();
+      continue;
     }
     // ---- 3. multiple Arnoldi basis, with the projection accumulated on the way ---------
     T* Lv = V0;
@@ -1188,6 +1330,11 @@ mka_status launch_t(const mka_system* sys, const AtomsConfig& cf, const AtomsLau
   A.vp = a.vp;
   A.blk_off = a.blk_off;
   A.self_k = a.self_k;
+  A.x0 = a.x0;
+  A.patch = a.patch;
+  A.fallback = a.fallback;
+  A.cg_only = a.cg_only;
+  A.cg_target = a.cg_target;
   atoms_kernel<TV, T, NT><<<(unsigned)a.grid, NT, cf.smem, st>>>(A);
   count_launches();
   MKA_CUDA_TRY(cudaGetLastError());
@@ -1249,6 +1396,23 @@ mka_status launch_columns(mka_system* sys, mka_result* res, const mka_solve_para
   MKA_CUDA_TRY(cudaMallocAsync(&counter, sizeof(int), st));
   MKA_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
   AtomsLaunchArgs a{};
+  // learned warm start: features, then the network's prediction of s_j on each patch
+  float* wbuf = nullptr;
+  int32_t* patch = nullptr;
+  if (prm->use_warm_start) {
+    const int64_t rows = 4 * res->n_sel;
+    MKA_CUDA_TRY(cudaMallocAsync(&wbuf, sizeof(float) * (rows * (132 + 68) + mlp_work_floats(rows)), st));
+    MKA_CUDA_TRY(cudaMallocAsync(&patch, sizeof(int32_t) * 17 * res->n_sel, st));
+    float* X = wbuf;
+    float* Y = X + rows * 132;
+    float* W = Y + rows * 68;
+    s = features_enqueue(sys, res->d_sel, res->n_sel, X, patch, st);
+    if (!s) s = mlp_forward_enqueue(sys->warm, X, rows, W, W + rows * 128, W + 2 * rows * 128, W + 3 * rows * 128, Y, st);
+    if (s) return s;
+    a.x0 = Y;
+    a.patch = patch;
+    a.fallback = res->d_fallback;
+  }
   a.sel = res->d_sel;
   a.order = nullptr;
   a.n_sel = res->n_sel;
@@ -1271,6 +1435,8 @@ mka_status launch_columns(mka_system* sys, mka_result* res, const mka_solve_para
   s = atoms_launch(sys, prm->arith, cf, a, st);
   cudaFreeAsync(scratch, st);
   cudaFreeAsync(counter, st);
+  if (wbuf) cudaFreeAsync(wbuf, st);
+  if (patch) cudaFreeAsync(patch, st);
   return s;
 }
 

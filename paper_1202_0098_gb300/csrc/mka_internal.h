@@ -48,6 +48,7 @@ struct mka_system {
   void* d_valS = nullptr;
   double* d_pos = nullptr;      // [n_atoms][3], wrapped into the box
   float* d_posf = nullptr;      // the same rounded to FP32 (distance prefilter)
+  mka_mlp* warm = nullptr;      // network used when a solve asks for the learned warm start (not owned)
   int max_cluster = -1;         // largest cluster over all atoms (-1: not computed yet)
   mka::CellList cells{};
   // host copies of the pattern
@@ -72,6 +73,7 @@ struct mka_result {
   double* d_vp = nullptr;         // kept pattern rows [n_blocks][4 c][4 r][nu]
   int32_t* d_self = nullptr;      // [n_sel] index (within the atom's row) of its diagonal block
   double* d_mu_state = nullptr;   // bisection bracket and partial sums
+  int32_t* d_fallback = nullptr;  // [n_cols] warm-start fallback flags (learned start only)
   std::vector<int64_t> h_sel;
   std::vector<int64_t> h_blk_off;
 };
@@ -109,7 +111,19 @@ struct AtomsLaunchArgs {
   char* scratch = nullptr;         // grid x slot_bytes
   int* counter = nullptr;          // zero in stream order before the launch
   int grid = 0;
+  const float* x0 = nullptr;       // learned CG start on the patch [4 n_sel][68], or NULL
+  const int32_t* patch = nullptr;  // [n_sel][17]
+  int32_t* fallback = nullptr;     // [4 n_sel] or NULL
+  int cg_only = 0;                 // 1: stop after CG, write s_j on the patch into cg_target
+  float* cg_target = nullptr;      // [4 n_sel][68]
 };
+
+// Learned warm start (mlp.cu).
+mka_status features_enqueue(const mka_system* sys, const int64_t* d_sel, int64_t n, float* X, int32_t* patch,
+                            cudaStream_t st);
+mka_status mlp_forward_enqueue(const mka_mlp* net, const float* X, int64_t B, float* Z1, float* H1, float* Z2,
+                               float* H2, float* Y, cudaStream_t st);
+int64_t mlp_work_floats(int64_t B);   // floats of forward/backward work buffers for B rows
 
 mka_status atoms_config(const mka_system* sys, int nu, int arith, int max_cl, int threads, int ctas_per_sm,
                         AtomsConfig* out);

@@ -88,6 +88,8 @@ struct mka_plan {
   cudaEvent_t staged = nullptr;
   cudaStream_t capture = nullptr;  // private stream the graphs are captured on (never executes work)
   cudaEvent_t k0 = nullptr, k1 = nullptr;   // recorded around the per-atom kernel inside every graph
+  float* warm = nullptr;           // learned start: X [4A][132], Y [4A][68], network work buffers
+  int32_t* patch = nullptr;        // [A][17]
   std::vector<mka::GraphEntry> graphs;
 };
 
@@ -128,6 +130,11 @@ mka_status plan_alloc(mka_plan* P) {
   MKA_CUDA_TRY(cudaStreamCreateWithFlags(&P->capture, cudaStreamNonBlocking));
   MKA_CUDA_TRY(cudaEventCreate(&P->k0));
   MKA_CUDA_TRY(cudaEventCreate(&P->k1));
+  if (P->prm.use_warm_start) {
+    MKA_CUDA_TRY(cudaMalloc(&r->d_fallback, sizeof(int32_t) * 4 * A));
+    MKA_CUDA_TRY(cudaMalloc(&P->warm, sizeof(float) * (4 * A * (132 + 68) + mlp_work_floats(4 * A))));
+    MKA_CUDA_TRY(cudaMalloc(&P->patch, sizeof(int32_t) * 17 * A));
+  }
   return MKA_OK;
 }
 
@@ -153,6 +160,18 @@ mka_status plan_enqueue(mka_plan* P, int64_t n, double n_electrons, double kT, d
     order = P->order;
   }
   AtomsLaunchArgs a{};
+  if (P->prm.use_warm_start) {
+    const int64_t rows = 4 * n;
+    float* X = P->warm;
+    float* Y = X + 4 * P->max_atoms * 132;
+    float* W = Y + 4 * P->max_atoms * 68;
+    mka_status sw = features_enqueue(P->sys, r->d_sel, n, X, P->patch, st);
+    if (!sw) sw = mlp_forward_enqueue(P->sys->warm, X, rows, W, W + rows * 128, W + 2 * rows * 128, W + 3 * rows * 128, Y, st);
+    if (sw) return sw;
+    a.x0 = Y;
+    a.patch = P->patch;
+    a.fallback = r->d_fallback;
+  }
   a.sel = r->d_sel;
   a.order = order;
   a.n_sel = n;
@@ -202,6 +221,8 @@ void mka_plan_destroy(mka_plan* P) {
   cudaFree(P->bins);
   cudaFree(P->mu_buf);
   cudaFree(P->dev_out);
+  cudaFree(P->warm);
+  cudaFree(P->patch);
   mka_result_destroy(P->res);
   delete P;
 }
@@ -216,7 +237,8 @@ mka_status mka_plan_create(mka_system* sys, int64_t max_atoms, const mka_solve_p
   if (prm->arith != MKA_FP64 && prm->arith != MKA_MIXED_FP32)
     return fail(MKA_ERR_INVALID_ARG, "arith must be MKA_FP64 or MKA_MIXED_FP32");
   if (!(prm->cg_tol > 0) || prm->cg_maxit < 1) return fail(MKA_ERR_INVALID_ARG, "need cg_tol > 0, cg_maxit >= 1");
-  if (prm->use_warm_start) return fail(MKA_ERR_INVALID_ARG, "plans run without a warm start");
+  if (prm->use_warm_start && !sys->warm)
+    return fail(MKA_ERR_INVALID_ARG, "use_warm_start needs a network attached with mka_system_set_warm_start");
   mka_tuning t{256, 0, 0};
   if (tune) t = *tune;
   if (t.threads == 0) t.threads = 256;

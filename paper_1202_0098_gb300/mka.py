@@ -30,7 +30,10 @@ EXPORTED = [
     "mka_system_destroy", "mka_spmv", "mka_solve_columns", "mka_solve_columns_static", "mka_result_info", "mka_result_copy_levels",
     "mka_result_device_levels", "mka_result_destroy", "mka_find_mu", "mka_density_energy", "mka_greens",
     "mka_plan_create", "mka_plan_run", "mka_plan_scalars", "mka_plan_kernel_ms", "mka_plan_result", "mka_plan_info", "mka_plan_destroy",
-    "mka_autotune", "mka_kernel_launches", "mka_last_error", "mka_status_string",
+    "mka_autotune", "mka_mlp_num_params", "mka_mlp_create", "mka_mlp_destroy", "mka_mlp_set_params",
+    "mka_mlp_get_params", "mka_mlp_forward", "mka_mlp_gradients", "mka_mlp_train_step", "mka_warm_start_features",
+    "mka_cg_patch_targets", "mka_system_set_warm_start", "mka_result_copy_warm_start",
+    "mka_kernel_launches", "mka_last_error", "mka_status_string",
 ]
 
 
@@ -93,6 +96,16 @@ def load(path: str | None = None) -> C.CDLL:
         "mka_plan_kernel_ms": [P, P],
         "mka_plan_info": [P, P, P, P],
         "mka_autotune": [P, P, P, I64, D, D, C.c_char_p, P, P],
+        "mka_mlp_create": [C.c_uint64, P],
+        "mka_mlp_set_params": [P, P],
+        "mka_mlp_get_params": [P, P, I32],
+        "mka_mlp_forward": [P, P, P, I64, P],
+        "mka_mlp_gradients": [P, P, P, I64, P, P, P],
+        "mka_mlp_train_step": [P, P, P, I64, C.c_float, P, P],
+        "mka_warm_start_features": [P, P, I64, P, P, P],
+        "mka_cg_patch_targets": [P, P, I64, I32, D, P, P, P, P],
+        "mka_system_set_warm_start": [P, P],
+        "mka_result_copy_warm_start": [P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -100,6 +113,10 @@ def load(path: str | None = None) -> C.CDLL:
         f.restype = C.c_int
     lib.mka_system_destroy.argtypes = [P]
     lib.mka_system_destroy.restype = None
+    lib.mka_mlp_num_params.argtypes = []
+    lib.mka_mlp_num_params.restype = C.c_int64
+    lib.mka_mlp_destroy.argtypes = [P]
+    lib.mka_mlp_destroy.restype = None
     lib.mka_plan_destroy.argtypes = [P]
     lib.mka_plan_destroy.restype = None
     lib.mka_result_destroy.argtypes = [P]
@@ -335,6 +352,78 @@ def mka_autotune(sys, prm: mka_solve_params, sample: np.ndarray, n_electrons: fl
     _check(load().mka_autotune(sys, C.byref(prm), _ptr(a), a.shape[0], float(n_electrons), float(kT),
                                cache_path.encode() if cache_path else None, C.c_void_p(stream), C.byref(out)),
            "mka_autotune")
+    return out
+
+
+# ---- learned warm start ------------------------------------------------------------------
+
+def mka_mlp_num_params() -> int:
+    return int(load().mka_mlp_num_params())
+
+
+def mka_mlp_create(seed: int = 0) -> C.c_void_p:
+    out = C.c_void_p()
+    _check(load().mka_mlp_create(C.c_uint64(seed), C.byref(out)), "mka_mlp_create")
+    return out
+
+
+def mka_mlp_destroy(net):
+    if net:
+        load().mka_mlp_destroy(net)
+
+
+def mka_mlp_set_params(net, params: np.ndarray):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(load().mka_mlp_set_params(net, _ptr(p)), "mka_mlp_set_params")
+
+
+def mka_mlp_get_params(net, bf16_rounded: bool = False) -> np.ndarray:
+    p = np.empty(mka_mlp_num_params(), np.float32)
+    _check(load().mka_mlp_get_params(net, _ptr(p), int(bf16_rounded)), "mka_mlp_get_params")
+    return p
+
+
+def mka_mlp_forward(net, x_ptr: int, y_ptr: int, B: int, stream: int = 0):
+    _check(load().mka_mlp_forward(net, C.c_void_p(x_ptr), C.c_void_p(y_ptr), B, C.c_void_p(stream)), "mka_mlp_forward")
+
+
+def mka_mlp_gradients(net, x_ptr: int, t_ptr: int, B: int, grad_ptr: int | None, loss_ptr: int | None,
+                      stream: int = 0):
+    V = C.c_void_p
+    _check(load().mka_mlp_gradients(net, V(x_ptr), V(t_ptr), B, V(grad_ptr) if grad_ptr else None,
+                                    V(loss_ptr) if loss_ptr else None, V(stream)), "mka_mlp_gradients")
+
+
+def mka_mlp_train_step(net, x_ptr: int, t_ptr: int, B: int, lr: float, loss_ptr: int | None = None,
+                       stream: int = 0):
+    V = C.c_void_p
+    _check(load().mka_mlp_train_step(net, V(x_ptr), V(t_ptr), B, C.c_float(lr), V(loss_ptr) if loss_ptr else None,
+                                     V(stream)), "mka_mlp_train_step")
+
+
+def mka_warm_start_features(sys, atoms: np.ndarray, x_ptr: int, patch_ptr: int, stream: int = 0):
+    a = np.ascontiguousarray(atoms, dtype=np.int64)
+    _check(load().mka_warm_start_features(sys, _ptr(a), a.shape[0], C.c_void_p(x_ptr), C.c_void_p(patch_ptr),
+                                          C.c_void_p(stream)), "mka_warm_start_features")
+
+
+def mka_cg_patch_targets(sys, atoms: np.ndarray, arith: str, cg_tol: float, patch_ptr: int, y_ptr: int,
+                         iters_ptr: int | None = None, stream: int = 0):
+    a = np.ascontiguousarray(atoms, dtype=np.int64)
+    V = C.c_void_p
+    _check(load().mka_cg_patch_targets(sys, _ptr(a), a.shape[0], MKA_FP64 if arith == "fp64" else MKA_MIXED_FP32,
+                                       float(cg_tol), V(patch_ptr), V(y_ptr), V(iters_ptr) if iters_ptr else None,
+                                       V(stream)), "mka_cg_patch_targets")
+
+
+def mka_system_set_warm_start(sys, net):
+    _check(load().mka_system_set_warm_start(sys, net), "mka_system_set_warm_start")
+
+
+def mka_result_copy_warm_start(res) -> np.ndarray:
+    n = mka_result_info(res)["n_cols"]
+    out = np.empty(n, np.int32)
+    _check(load().mka_result_copy_warm_start(res, _ptr(out)), "mka_result_copy_warm_start")
     return out
 
 
