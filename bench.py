@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shape instead of the autotuner's")
+    ap.add_argument("--no-learned", action="store_true", help="mixed form without the learned CG start")
     return ap.parse_args()
 
 
@@ -214,11 +215,39 @@ def alu_roofline(f_vec, f_red, kernel_s, n_cols, form):
             "flops_per_column": {"vector": f_vec, "reduced_fp64": f_red}}
 
 
+def train_warm_start(mka, torch, seed=100):
+    """The learned CG start, trained with the library's kernels on 2e5 inner-CG solutions (50,000 atoms x 4
+    columns) of fresh seeds of the fcc (vacancies, sigma 0.08) and amorphous-like diamond (sigma 0.15) generators."""
+    from paper_1202_0098_gb300 import warm_start
+    from synth import SK_FCC_METAL, SK_CARBON_LIKE, lattice_positions
+    Xs, Ys = [], []
+    t0 = time.perf_counter()
+    gens = [("fcc", 4.0, 20, 0.08, 0.05, SK_FCC_METAL, 7.0), ("fcc", 4.0, 20, 0.08, 0.05, SK_FCC_METAL, 7.0),
+            ("diamond", 3.567, 16, 0.15, 0.0, SK_CARBON_LIKE, 7.0), ("diamond", 3.567, 16, 0.15, 0.0, SK_CARBON_LIKE, 7.0)]
+    for k, (lat, a, nc, sig, vac, skp, R) in enumerate(gens):
+        pos, box = lattice_positions(lat, a, nc, sig, vac, seed + k)
+        s = mka.mka_build_system(pos, box, skp, "bf16", cluster_radius=R)
+        atoms = np.sort(np.random.default_rng(seed + k).choice(pos.shape[0], 12500, replace=False)).astype(np.int64)
+        X, Y, _ = warm_start.collect(s, atoms, "mixed", 1e-7)
+        Xs.append(X)
+        Ys.append(Y)
+        mka.mka_system_destroy(s)
+    X, Y = torch.cat(Xs), torch.cat(Ys)
+    net = mka.mka_mlp_create(seed)
+    mse0 = warm_start.mse(net, X, Y)
+    hist = warm_start.train(net, X, Y, epochs=20, batch=1024, lr=1e-3, seed=seed)
+    info = {"samples": int(X.shape[0]), "generators": "fcc (config-2) and diamond sigma 0.15 (config-3), seeds "
+            f"{seed}-{seed + 3}", "epochs": 20, "batch": 1024, "mse_init": mse0, "mse_final": hist[-1],
+            "train_s": time.perf_counter() - t0}
+    del X, Y, Xs, Ys
+    return net, info
+
+
 def run_form(mka, torch, sysh, w, form, B, batch_atoms, steps, warmup, stream, tune_cache, rank, autotune=True,
-             compare=()):
+             compare=(), learned=False):
     """Time `steps` batches of one form through an autotuned plan (graph replay); returns timings + outputs."""
     cg_tol = 1e-12 if form == "fp64" else 1e-7
-    prm = mka.solve_params(w.p, w.q, arith=form, cg_tol=cg_tol, keep_vectors=True)
+    prm = mka.solve_params(w.p, w.q, arith=form, cg_tol=cg_tol, keep_vectors=True, use_warm_start=learned)
     sp = stream.cuda_stream
     if autotune:
         tune = mka.mka_autotune(sysh, prm, batch_atoms(0)[:min(B, 4096)], w.electrons_per_atom * min(B, 4096), w.kT,
@@ -253,6 +282,7 @@ def run_form(mka, torch, sysh, w, form, B, batch_atoms, steps, warmup, stream, t
         ebs.append(e)
     lv = mka.mka_result_copy_levels(mka.mka_plan_result(plan), check=False)
     out["mu"], out["e_band"], out["cg_iters"] = mus, ebs, float(lv["cg_iters"].mean())
+    out["fallback_rate"] = float(mka.mka_result_copy_warm_start(mka.mka_plan_result(plan)).mean()) if learned else None
     out["bad_columns"] = int(np.sum((lv["status"] != 0) & (lv["status"] != 4)))
     out["plan"], out["rho"], out["prm"] = plan, rho, prm
     return out
@@ -289,8 +319,13 @@ def main():
         return np.arange(start, start + B, dtype=np.int64) % N
 
     compare = list(range(args.warmup, args.warmup + max(1, min(args.steps, 3))))
+    learned = form == "mixed" and not args.no_learned
+    net, learn_info = (None, None)
+    if learned:
+        net, learn_info = train_warm_start(mka, torch)
+        mka.mka_system_set_warm_start(sysh, net)
     main_run = run_form(mka, torch, sysh, w, form, B, batch_atoms, args.steps, args.warmup, stream, tune_cache, rank,
-                        not args.no_autotune, compare)
+                        not args.no_autotune, compare, learned)
     ms = main_run["ms"]
     if world > 1:
         tt = torch.tensor([ms], device="cuda")
@@ -327,6 +362,26 @@ def main():
         e2e = {"value": 4 * B * args.steps * world / te, "unit": "columns/s", "h2d_bytes_per_step": 16 * B + 8,
                "d2h_bytes_per_step": d2h // args.steps}
 
+    # the mixed form without the learned start on the same batches: what the network gains
+    if learned:
+        fsteps = max(1, min(args.steps, 3))
+        prun = run_form(mka, torch, sysh, w, "mixed", B, batch_atoms, fsteps, 1, stream, tune_cache, rank,
+                        not args.no_autotune, compare, False)
+        pval = 4 * B * fsteps / (prun["ms"] / 1e3)
+        # both plans' rho buffers on the same (last compared) batch
+        last = batch_atoms(compare[-1])
+        mka.mka_plan_run(main_run["plan"], last, w.electrons_per_atom * B, w.kT, main_run["rho"].data_ptr())
+        torch.cuda.synchronize()
+        nb = mka.mka_result_info(mka.mka_plan_result(prun["plan"]))["n_blocks"]
+        learn_info.update({
+            "plain_mixed_value": pval, "speedup_over_plain_mixed": value / world / pval,
+            "cg_iters_plain": prun["cg_iters"], "cg_iters_learned": main_run["cg_iters"],
+            "fallback_rate": main_run["fallback_rate"],
+            "max_abs_drho_vs_plain": float((main_run["rho"][:nb * 16] - prun["rho"][:nb * 16]).abs().max().item()),
+            "max_abs_dE_eV_per_atom_vs_plain": max(abs(a - b) for a, b in zip(main_run["e_band"], prun["e_band"])) / B,
+            "max_abs_dmu_eV_vs_plain": max(abs(a - b) for a, b in zip(main_run["mu"], prun["mu"]))})
+        mka.mka_plan_destroy(prun["plan"])
+
     # the FP64 form on the same stored values and batches: speed and agreement of mu / E
     other = None
     if form != "fp64" and not args.no_fp64_compare:
@@ -344,7 +399,7 @@ def main():
 
     # roofline of the per-atom kernel from its in-graph event time
     from scipy.spatial import cKDTree
-    bsr = mka.mka_system_copy_bsr(sysh)
+    bsr = mka.mka_system_copy_bsr(sysh, values=False)
     tree = cKDTree(pos, boxsize=box)
     fv = fr = 0.0
     for i in range(args.warmup, n_steps):
@@ -358,20 +413,22 @@ def main():
     roofline = alu_roofline(fv, fr, kernel_s, 4 * B, form)
     mka.mka_plan_destroy(plan)
     mka.mka_system_destroy(sysh)
+    if net is not None:
+        mka.mka_mlp_destroy(net)
 
     line = {"metric": "density-matrix columns/s", "value": value, "unit": "columns/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if form == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {N} atoms, {4 * N} columns, R={w.R} A, p=q={w.p}, "
-                                   f"kT={w.kT} eV, {form} form, {storage}-stored H and S",
+                                   f"kT={w.kT} eV, {form}{'+learned' if learned else ''} form, {storage}-stored H and S",
                        "atoms_per_step": B, "columns_per_step": 4 * B,
                        "step": "one graph-replayed batch: per-atom kernel, mu bisection over the batch, rho, E",
                        "l2": "inputs larger than L2 (H,S of the whole system in HBM; each step a new batch of atoms)",
                        "tuning": main_run["tuning"], "build_s": t_build},
             "gpu_launches": main_run["launches"], "clocks": clk, "e2e": e2e, "roofline": roofline,
             "kernel_ms_mean": statistics.mean(main_run["kernel_ms"]), "cg_iters_mean": main_run["cg_iters"],
-            "bad_columns": main_run["bad_columns"], "fp64_form": other,
+            "bad_columns": main_run["bad_columns"], "learned_warm_start": learn_info, "fp64_form": other,
             "mu_first_compared": main_run["mu"][0], "e_band_per_atom_first_compared": main_run["e_band"][0] / B}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, pos, box)

@@ -7,14 +7,16 @@
 //   1. cluster extraction: atoms within R of a (minimum image) from the cell
 //      list, sorted by atom id; the cluster-local 4x4-block pattern of
 //      P H P / P S P is built in shared memory (local column, global block id);
-//   2. inner CG for S s_j = e_j (Sec. 2, standard CG, x0 = 0);
+//   2. inner CG for S s_j = e_j (Sec. 2, standard CG, from x0 = 0 or from a
+//      learned guess on the 17-atom patch);
 //   3. the S-orthonormal basis of K_p(H; e_j) (+) K_q(H; s_j): S-orthogonalise,
 //      normalise, k_n = H u_n, next vector k_n or s_j after u_p (Eqs.
 //      EQ-REC-UN, EQ-KN-HUN, EQ-MGram-Schmidt, EQ-CALC-S-INV); Gram-Schmidt is
 //      the classical form run twice, coefficients (S u_m)^T l with S u_m kept;
-//   4. the projection H_r = U^T K, S_r = U^T (S U), symmetrised, and the
-//      reduced generalized problem (Eq. EQ-SUB-EIG-VEC): Cholesky of S_r,
-//      L^{-1} H_r L^{-T}, parallel cyclic Jacobi eigensolve, C = L^{-T} Y;
+//   4. the projection H_r = U^T K, S_r = U^T (S U), accumulated while the basis
+//      grows, and the reduced generalized problem (Eq. EQ-SUB-EIG-VEC), one
+//      warp per column in FP64: Cholesky of S_r, L^{-1} H_r L^{-T}, Householder
+//      tridiagonalisation, implicit QL, C = L^{-T} Y;
 //   5. per column: ascending eps_alpha, w_alpha = V_{j alpha} (S V)_{j alpha},
 //      and (optionally) the pattern rows of V for rho and G.
 // Breakdown rule: a new vector that keeps no more than 1e-10 of its S-norm
@@ -22,12 +24,24 @@
 // coefficients) is dropped; a dropped s_j is replaced by H u_n, a first chain
 // that closes before u_p hands over to s_j, any other breakdown ends the basis.
 //
-// Vectors (U, S U, K = H U and the CG/Arnoldi work vectors) live in a per-CTA
-// global scratch slot, [row][4 columns] interleaved so that one thread owns a
-// row of all four columns; the cluster pattern, reductions and the nu x nu
-// matrices live in shared memory. Arithmetic type T is double for the FP64
-// form and float for the mixed form (values of any storage type are decoded
-// to T on load); the projection and the reduced solve are FP64 in both.
+// The work vectors (CG: p, S p, r; basis: l, S l, H u) live in shared memory,
+// [row][4 columns] interleaved so that one thread owns a row of all four
+// columns; the basis U and S U, s_j and the projected matrices live in a
+// per-CTA global slot. Arithmetic type T is double for the FP64 form and float
+// for the mixed form (values of any storage type are decoded to T on load).
+//
+// Mixed form. s_j is nearly inside K_p(H; e_j): the seam vector keeps about 1%
+// of its S-norm, so any perturbation of the first chain at FP32 rounding level
+// turns the direction the second chain starts from by about 100 times as much.
+// The basis is therefore carried as FP32 pairs (hi + lo, about 48 significant
+// bits): H u and S u take error-free FP32 products and compensated sums on the
+// hi part, the Gram-Schmidt update likewise, and only products with the lo
+// parts are rounded. s_j is refined to FP64 accuracy by CG on the true residual
+// (computed the same way) and orthogonalised in FP64 at the seam. The
+// Gram-Schmidt coefficients and the projected matrices are taken from the hi
+// parts (their errors stay inside the span or enter the reduced problem
+// unmagnified); the reduced solve, the mu bisection and all cross-thread sums
+// are FP64.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -354,6 +368,92 @@ __device__ void resid4_comp(const TV* __restrict__ val, const int* lrow, const u
     for (int q = 0; q < 4; ++q) {
       const float e = (row == jrow0 + q) ? 1.0f : 0.0f;
       r[4 * row + q] = __fsub_rn(__fsub_rn(e, hi[q]), lo[q]);
+    }
+  }
+  __syncthreads();
+}
+
+// r = e_j - A (hi + lo) for x given as an FP32 pair: the hi part with error-free products and
+// compensated sums as in resid4_comp, the small lo part (|lo| <= ulp(hi) / 2) in plain FP32.
+template <typename TV>
+__device__ void resid4_comp2(const TV* __restrict__ val, const int* lrow, const uint16_t* lcol, const int* lblk,
+                             int ncl, const float* __restrict__ xh, const float* __restrict__ xl, float* __restrict__ r,
+                             int jrow0) {
+  for (int row = threadIdx.x; row < 4 * ncl; row += blockDim.x) {
+    const int t = row >> 2, i = row & 3;
+    float hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0}, sl[4] = {0, 0, 0, 0};
+    for (int e = lrow[t]; e < lrow[t + 1]; ++e) {
+      float v[4];
+      RowLoad<TV, float>::load(val, lblk[e], i, v);
+      const float* xb = xh + (size_t)lcol[e] * 16;
+      const float* xc = xl + (size_t)lcol[e] * 16;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float xk[4], xs[4];
+        ld4(xb + 4 * k, xk);
+        ld4(xc + 4 * k, xs);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float p = __fmul_rn(v[k], xk[q]);
+          const float pe = fmaf(v[k], xk[q], -p);
+          const float s = __fadd_rn(hi[q], p);
+          const float bb = __fsub_rn(s, hi[q]);
+          const float err = __fadd_rn(__fsub_rn(hi[q], __fsub_rn(s, bb)), __fsub_rn(p, bb));
+          hi[q] = s;
+          lo[q] = __fadd_rn(lo[q], __fadd_rn(err, pe));
+          sl[q] = fmaf(v[k], xs[q], sl[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float e = (row == jrow0 + q) ? 1.0f : 0.0f;
+      r[4 * row + q] = __fsub_rn(__fsub_rn(__fsub_rn(e, hi[q]), lo[q]), sl[q]);
+    }
+  }
+  __syncthreads();
+}
+
+// y = A x for x given as an FP32 pair (xh + xl), the result as an FP32 pair (yh + yl), for the
+// columns in `mask`: the hi part with error-free products and compensated sums, the lo part in
+// plain FP32, renormalised so that yh is the sum rounded to FP32 and |yl| <= ulp(yh) / 2
+// (yl == nullptr: yh only). Other columns are left untouched.
+template <typename TV>
+__device__ void spmm4_pair(const TV* __restrict__ val, const int* lrow, const uint16_t* lcol, const int* lblk,
+                           int ncl, const float* __restrict__ xh, const float* __restrict__ xl, float* __restrict__ yh,
+                           float* __restrict__ yl, int mask) {
+  for (int row = threadIdx.x; row < 4 * ncl; row += blockDim.x) {
+    const int t = row >> 2, i = row & 3;
+    float hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
+    const int e1 = lrow[t + 1];
+    for (int e = lrow[t]; e < e1; ++e) {
+      float v[4];
+      RowLoad<TV, float>::load(val, lblk[e], i, v);
+      const float* xb = xh + (size_t)lcol[e] * 16;
+      const float* xc = xl + (size_t)lcol[e] * 16;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float xk[4], xs[4];
+        ld4(xb + 4 * k, xk);
+        ld4(xc + 4 * k, xs);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float p = __fmul_rn(v[k], xk[q]);
+          const float pe = fmaf(v[k], xk[q], -p);
+          const float s = __fadd_rn(hi[q], p);
+          const float bb = __fsub_rn(s, hi[q]);
+          const float err = __fadd_rn(__fsub_rn(hi[q], __fsub_rn(s, bb)), __fsub_rn(p, bb));
+          hi[q] = s;
+          lo[q] = __fadd_rn(lo[q], __fadd_rn(err, fmaf(v[k], xs[q], pe)));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (!(mask >> q & 1)) continue;
+      const float s = __fadd_rn(hi[q], lo[q]);
+      yh[4 * row + q] = s;
+      if (yl) yl[4 * row + q] = __fsub_rn(lo[q], __fsub_rn(s, hi[q]));
     }
   }
   __syncthreads();
@@ -735,6 +835,9 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
   T* V0 = reinterpret_cast<T*>(region);     // CG: p     basis: l
   T* V1 = V0 + (size_t)m_cap * 4;           // CG: S p   basis: S l, then S u_{n-1}
   T* V2 = V1 + (size_t)m_cap * 4;           // CG: r     basis: H u_{n-1}
+  // FP32 form only: the low halves of l and H u_{n-1}
+  float* Llo = reinterpret_cast<float*>(V2 + (size_t)m_cap * 4);
+  float* Klo = Llo + (size_t)m_cap * 4;
   double* RM = reinterpret_cast<double*>(region);   // per column: H_r / C (nu x ld), S_r / L, 8 nu scratch
   const size_t rm_col = (size_t)2 * nu * ld + red_scratch_doubles(nu);
 
@@ -743,6 +846,13 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
   T* SU = U + (size_t)nu * m_cap * 4;                // [nu][m_cap][4]
   T* SJ = SU + (size_t)nu * m_cap * 4;               // s_j, [m_cap][4]
   double* HS = reinterpret_cast<double*>(slot + align_up(sizeof(T) * ((size_t)2 * nu + 1) * m_cap * 4, 256));
+  double* SJd = reinterpret_cast<double*>(reinterpret_cast<char*>(HS) + align_up(sizeof(double) * 8 * (size_t)nu * nu, 256));
+  (void)SJd;   // FP32 arithmetic only: s_j in FP64 for the seam [m_cap][4]
+  // FP32 arithmetic only: low halves of the basis vectors [nu][m_cap][4]
+  float* Ulo = reinterpret_cast<float*>(reinterpret_cast<char*>(SJd) + align_up(sizeof(double) * 4 * (size_t)m_cap, 256));
+  (void)Ulo;
+  (void)Llo;
+  (void)Klo;
 
   for (;;) {
     if (threadIdx.x == 0) {
@@ -870,25 +980,35 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
       st.cg_active[threadIdx.x] = sqrt(st.rr[threadIdx.x]) > A.cg_tol;
     }
     __syncthreads();
-    // Phase 0: CG to the tolerance. Phase 1 (FP32 arithmetic only): the true residual of x,
-    // recomputed with error-free products and compensated sums, replaces the recursive one and
-    // CG continues until it has dropped 30-fold, which takes x to FP32 rounding accuracy (the
-    // seam vector s_j lies mostly inside K_p(H; e_j), so its error would otherwise be magnified).
-    constexpr int kPhases = sizeof(T) == 4 ? 2 : 1;
+    // Phase 0: CG to the tolerance. Phases 1 and 2 (FP32 arithmetic only): x is carried in FP64,
+    // its true residual, recomputed with error-free products and compensated sums (x as an FP32
+    // pair), replaces the recursive one and CG on the correction continues until the residual has
+    // dropped 1000-fold; two such rounds leave s_j accurate far below FP32 rounding. The seam
+    // vector is s_j minus its projection on K_p(H; e_j), of which s_j is mostly made, so its
+    // relative accuracy is that of s_j divided by the small remainder.
+    constexpr int kPhases = sizeof(T) == 4 ? 3 : 1;
     for (int phase = 0; phase < kPhases; ++phase) {
       int maxit = A.cg_maxit;
-      if (phase == 1) {
+      if (phase >= 1) {
         maxit = 20;
-        for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) P[i] = SJ[i];
+        if (phase == 1)
+          for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) SJd[i] = (double)SJ[i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
+          const double x = SJd[i];
+          const T h = (T)x;
+          P[i] = h;
+          AP[i] = (T)(x - (double)h);
+        }
         __syncthreads();
         if constexpr (sizeof(T) == 4)
-          resid4_comp<TV>(A.valS, lrow, lcol, lblk, ncl, reinterpret_cast<const float*>(P),
-                          reinterpret_cast<float*>(R), 4 * t0);
+          resid4_comp2<TV>(A.valS, lrow, lcol, lblk, ncl, reinterpret_cast<const float*>(P),
+                           reinterpret_cast<const float*>(AP), reinterpret_cast<float*>(R), 4 * t0);
         dot4<T>(R, R, m, red, sums);
         if (threadIdx.x < 4) {
           const int c = threadIdx.x;
           st.rr[c] = sums[c];
-          st.cg_stop[c] = 3e-2 * sqrt(sums[c]);
+          st.cg_stop[c] = 1e-3 * sqrt(sums[c]);
           st.cg_active[c] = (st.status[c] == ST_OK) && sums[c] > 0.0;
         }
         __syncthreads();
@@ -919,7 +1039,8 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
           const int c = i & 3;
           if (st.cg_active[c]) {
             const T a = scal[c];
-            SJ[i] += a * P[i];
+            if (phase == 0) SJ[i] += a * P[i];
+            else SJd[i] += st.alpha[c] * (double)P[i];
             R[i] -= a * AP[i];
           }
         }
@@ -950,6 +1071,9 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
       }
       __syncthreads();
     }
+    if (sizeof(T) == 4)
+      for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) SJ[i] = (T)SJd[i];
+    __syncthreads();
     if (A.fallback && threadIdx.x < 4) A.fallback[4 * widx + threadIdx.x] = st.act[threadIdx.x];
     if (A.cg_only) {
       for (int i = threadIdx.x; i < 4 * 68; i += blockDim.x) {
@@ -985,6 +1109,7 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
     for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
       const int r = i >> 2, c = i & 3;
       Lv[i] = (r == 4 * t0 + c) ? (T)1 : (T)0;
+      if constexpr (sizeof(T) == 4) Llo[i] = 0.0f;
     }
     __syncthreads();
     for (int guard = 0; guard < nu + 4; ++guard) {
@@ -1010,14 +1135,91 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
         if (threadIdx.x == 0) st.proj_any = 0;
         for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
           const int r = i >> 2, c = i & 3;
+          if constexpr (sizeof(T) == 4) {
+            if (st.active[c]) {
+              // l and the basis as FP32 pairs, the update with error-free products and
+              // compensated sums; only the low parts' products are rounded
+              float h = Lv[i], lo = Llo[i];
+              const int nc = min(nmax, st.n[c]);
+              for (int mm = 0; mm < nc; ++mm) {
+                const size_t o = (size_t)mm * m_cap * 4 + 4 * r + c;
+                const float cf = coefT[mm * 4 + c];
+                const float uh = U[o];
+                const float p = __fmul_rn(cf, uh);
+                const float pe = fmaf(cf, uh, -p);
+                const float s = __fsub_rn(h, p);
+                const float bb = __fsub_rn(s, h);
+                const float err = __fsub_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fadd_rn(p, bb));
+                h = s;
+                lo = __fsub_rn(__fadd_rn(lo, err), fmaf(cf, Ulo[o], pe));
+              }
+              const float s = __fadd_rn(h, lo);
+              Lv[i] = s;
+              Llo[i] = __fsub_rn(lo, __fsub_rn(s, h));
+              continue;
+            }
+          }
           T v = Lv[i];
           for (int mm = 0; mm < nmax; ++mm) v -= coefT[mm * 4 + c] * U[(size_t)mm * m_cap * 4 + 4 * r + c];
           Lv[i] = v;
         }
         __syncthreads();
       }
+      if constexpr (sizeof(T) == 4) {
+        // the seam vector in FP64: two classical Gram-Schmidt passes on s_j (FP64) for the columns
+        // whose l is s_j, replacing what the FP32 passes above made of them
+        const int smask = (st.active[0] && st.src[0] == SRC_S) | ((st.active[1] && st.src[1] == SRC_S) << 1) |
+                          ((st.active[2] && st.src[2] == SRC_S) << 2) | ((st.active[3] && st.src[3] == SRC_S) << 3);
+        if (smask && nmax > 0) {
+          const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+          if (threadIdx.x < 4) st.csum[threadIdx.x] = (smask >> threadIdx.x & 1) ? 0.0 : st.csum[threadIdx.x];
+          __syncthreads();
+          for (int pass = 0; pass < 2; ++pass) {
+            for (int mm = wid; mm < nmax; mm += nwarp) {
+              const T* su = SU + (size_t)mm * m_cap * 4;
+              double acc[4] = {0, 0, 0, 0};
+              for (int r = lane; r < m; r += 32)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  if (smask >> q & 1) acc[q] += (double)su[4 * r + q] * SJd[4 * r + q];
+#pragma unroll
+              for (int q = 0; q < 4; ++q) acc[q] = warp_sum(acc[q]);
+              if (lane < 4) coef[mm * 4 + lane] = ((smask >> lane & 1) && mm < st.n[lane]) ? acc[lane] : 0.0;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
+              const int r = i >> 2, q = i & 3;
+              if (!(smask >> q & 1)) continue;
+              double v = SJd[i];
+              for (int mm = 0; mm < nmax; ++mm) {
+                const size_t o = (size_t)mm * m_cap * 4 + 4 * r + q;
+                const double cf = coef[mm * 4 + q];
+                if (cf != 0.0) v -= cf * ((double)U[o] + (double)Ulo[o]);
+              }
+              SJd[i] = v;
+            }
+            if (threadIdx.x < 4 && (smask >> threadIdx.x & 1)) {
+              double s2 = 0;
+              for (int mm = 0; mm < nmax; ++mm) s2 += coef[mm * 4 + threadIdx.x] * coef[mm * 4 + threadIdx.x];
+              st.csum[threadIdx.x] += s2;
+            }
+            __syncthreads();
+          }
+          for (int i = threadIdx.x; i < 4 * m; i += blockDim.x)
+            if (smask >> (i & 3) & 1) {
+              const T h = (T)SJd[i];
+              Lv[i] = h;
+              Llo[i] = (float)(SJd[i] - (double)h);
+            }
+          __syncthreads();
+        }
+      }
       const int amask = st.active[0] | (st.active[1] << 1) | (st.active[2] << 2) | (st.active[3] << 3);
-      spmm4<TV, T>(A.valS, lrow, lcol, lblk, ncl, Lv, SL, amask);
+      // S l; in the FP32 form from the pair, rounded once, so that S_r is the Gram matrix of the basis kept
+      if constexpr (sizeof(T) == 4)
+        spmm4_pair<TV>(A.valS, lrow, lcol, lblk, ncl, Lv, Llo, SL, nullptr, amask);
+      else
+        spmm4<TV, T>(A.valS, lrow, lcol, lblk, ncl, Lv, SL, amask);
       dot4<T>(Lv, SL, m, red, sums);
       if (threadIdx.x < 4) {
         const int c = threadIdx.x;
@@ -1050,9 +1252,17 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
           const int r = i >> 2, c = i & 3;
           if (st.accept[c]) {
             const T bi = scal[8 + c];
-            const T u = Lv[i] * bi;
+            T u = Lv[i] * bi;
             const T su = SL[i] * bi;
             const size_t o = (size_t)st.n[c] * m_cap * 4 + 4 * r + c;
+            if constexpr (sizeof(T) == 4) {   // u_n as an FP32 pair
+              const float ul = __fadd_rn(fmaf(Lv[i], bi, -u), __fmul_rn(Llo[i], bi));
+              const float s = __fadd_rn(u, ul);
+              const float lo = __fsub_rn(ul, __fsub_rn(s, u));
+              u = s;
+              Ulo[o] = lo;
+              Llo[i] = lo;
+            }
             U[o] = u;
             SU[o] = su;
             Lv[i] = u;
@@ -1060,7 +1270,11 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
           }
         }
         __syncthreads();
-        spmm4<TV, T>(A.valH, lrow, lcol, lblk, ncl, Lv, KV, acc_mask);   // H u_n, accepted columns only
+        // H u_n, accepted columns only (as an FP32 pair in the FP32 form)
+        if constexpr (sizeof(T) == 4)
+          spmm4_pair<TV>(A.valH, lrow, lcol, lblk, ncl, Lv, Llo, KV, Klo, acc_mask);
+        else
+          spmm4<TV, T>(A.valH, lrow, lcol, lblk, ncl, Lv, KV, acc_mask);
       }
       if (threadIdx.x < 4) {
         const int c = threadIdx.x;
@@ -1086,10 +1300,13 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
         if (!st.active[c]) continue;
         if (st.accept[c]) {
           Lv[i] = st.next_s[c] ? SJ[i] : KV[i];
+          if constexpr (sizeof(T) == 4) Llo[i] = st.next_s[c] ? 0.0f : Klo[i];
         } else if (st.act[c] == ACT_LOAD_K) {
           Lv[i] = KV[i];
+          if constexpr (sizeof(T) == 4) Llo[i] = Klo[i];
         } else if (st.act[c] == ACT_LOAD_S) {
           Lv[i] = SJ[i];
+          if constexpr (sizeof(T) == 4) Llo[i] = 0.0f;
         }
       }
       __syncthreads();
@@ -1270,15 +1487,17 @@ size_t dyn_smem_bytes(int nu, int lnnz_cap, int mcap, size_t elem) {
   size_t off = (size_t)(2 * kMaxCl + 1 + lnnz_cap) * sizeof(int) + (size_t)lnnz_cap * sizeof(uint16_t);
   off = align_up(off, 16);
   const int ld = nu + 1;
-  const size_t vec = (size_t)3 * mcap * 4 * elem;
+  const size_t vec = (size_t)(elem == 4 ? 5 : 3) * mcap * 4 * elem;
   const size_t red = sizeof(double) * 4 * ((size_t)2 * nu * ld + red_scratch_doubles(nu));
   return off + std::max(vec, red);
 }
 
 // Per-CTA global work slot: U and S U ([nu][m_cap][4]) and s_j ([m_cap][4]) in the arithmetic
-// type, then H_r and S_r of the four columns (FP64, nu x nu each).
+// type, then H_r and S_r of the four columns (FP64, nu x nu each), then s_j in FP64 ([m_cap][4]),
+// then (FP32 arithmetic) the low halves of the basis vectors ([nu][m_cap][4] FP32).
 size_t slot_bytes_for(int nu, int mcap, size_t elem) {
-  return align_up(elem * ((size_t)2 * nu + 1) * mcap * 4, 256) + align_up(sizeof(double) * 8 * (size_t)nu * nu, 256);
+  return align_up(elem * ((size_t)2 * nu + 1) * mcap * 4, 256) + align_up(sizeof(double) * 8 * (size_t)nu * nu, 256) +
+         align_up(sizeof(double) * 4 * (size_t)mcap, 256) + (elem == 4 ? align_up(4 * (size_t)nu * mcap * 4, 256) : 0);
 }
 
 template <typename TV, typename T, int NT>

@@ -42,7 +42,9 @@ __device__ __forceinline__ float dsilu_f(float x) {
 // ---- features --------------------------------------------------------------------------
 struct FeatArgs {
   const double* pos;
-  double box[3];
+  const float* posf;
+  double box[3], inv_box[3];
+  float pre_hi;     // FP32 prefilter: candidates beyond pre_hi * r_gather^2 are dropped unseen
   int ncell[3];
   double cell_len[3];
   const int32_t* cell_start;
@@ -71,11 +73,13 @@ __device__ __forceinline__ int cell_range_f(int c, int n, int out[3]) {
 }
 
 // Minimum-image displacement and distance in the operation order of a plain evaluation
-// (d = b - a; d -= L rint(d / L); r^2 = (dx^2 + dy^2) + dz^2), without contraction, so that
-// neighbour order and the 3 A cut agree with any IEEE evaluation of the same formula.
-__device__ __forceinline__ double mi_comp(double pb, double pa, double L) {
+// (d = b - a; d -= L k with k = rint(d / L); r^2 = (dx^2 + dy^2) + dz^2), without contraction,
+// so that neighbour order and the 3 A cut agree with any IEEE evaluation of the same formula.
+// k is taken as rint(d * (1/L)): it differs from rint(d / L) only when d / L is within an ulp of
+// +-1/2, i.e. for atoms half a box away, far outside the gather radius.
+__device__ __forceinline__ double mi_comp(double pb, double pa, double L, double invL) {
   const double d = __dsub_rn(pb, pa);
-  return __dsub_rn(d, __dmul_rn(L, rint(__ddiv_rn(d, L))));
+  return __dsub_rn(d, __dmul_rn(L, rint(d * invL)));
 }
 
 // One warp per atom; per warp kFeatGather (distance, id) candidate slots in shared memory.
@@ -88,6 +92,10 @@ __global__ void __launch_bounds__(256) features_kernel(FeatArgs A) {
   for (int64_t t = warp; t < A.n_sel; t += nw) {
     const int64_t a = A.sel[t];
     const double px = A.pos[3 * a], py = A.pos[3 * a + 1], pz = A.pos[3 * a + 2];
+    const float pxf = A.posf[3 * a], pyf = A.posf[3 * a + 1], pzf = A.posf[3 * a + 2];
+    const float Lf[3] = {(float)A.box[0], (float)A.box[1], (float)A.box[2]};
+    const float iLf[3] = {(float)A.inv_box[0], (float)A.inv_box[1], (float)A.inv_box[2]};
+    const float rg2f = (float)A.r_gather2;
     int rx[3], ry[3], rz[3];
     const int nx = cell_range_f(cell_coord_f(px, A.cell_len[0], A.ncell[0]), A.ncell[0], rx);
     const int ny = cell_range_f(cell_coord_f(py, A.cell_len[1], A.ncell[1]), A.ncell[1], ry);
@@ -100,9 +108,14 @@ __global__ void __launch_bounds__(256) features_kernel(FeatArgs A) {
       for (int k = A.cell_start[c] + lane; k < A.cell_start[c + 1]; k += 32) {
         const int b = A.cell_atoms[k];
         if (b == a) continue;
-        const double dx = mi_comp(A.pos[3 * b], px, A.box[0]);
-        const double dy = mi_comp(A.pos[3 * b + 1], py, A.box[1]);
-        const double dz = mi_comp(A.pos[3 * b + 2], pz, A.box[2]);
+        float fx = A.posf[3 * b] - pxf, fy = A.posf[3 * b + 1] - pyf, fz = A.posf[3 * b + 2] - pzf;
+        fx -= Lf[0] * rintf(fx * iLf[0]);
+        fy -= Lf[1] * rintf(fy * iLf[1]);
+        fz -= Lf[2] * rintf(fz * iLf[2]);
+        if (fx * fx + fy * fy + fz * fz > A.pre_hi * rg2f) continue;
+        const double dx = mi_comp(A.pos[3 * b], px, A.box[0], A.inv_box[0]);
+        const double dy = mi_comp(A.pos[3 * b + 1], py, A.box[1], A.inv_box[1]);
+        const double dz = mi_comp(A.pos[3 * b + 2], pz, A.box[2], A.inv_box[2]);
         const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
         if (r2 <= A.r_gather2) {
           const int s = atomicAdd(&cnt[wid], 1);
@@ -144,9 +157,9 @@ __global__ void __launch_bounds__(256) features_kernel(FeatArgs A) {
       if (lane == k) {
         my_id = bid;
         if (best <= 3.0) {
-          const double dx = mi_comp(A.pos[3 * bid], px, A.box[0]);
-          const double dy = mi_comp(A.pos[3 * bid + 1], py, A.box[1]);
-          const double dz = mi_comp(A.pos[3 * bid + 2], pz, A.box[2]);
+          const double dx = mi_comp(A.pos[3 * bid], px, A.box[0], A.inv_box[0]);
+          const double dy = mi_comp(A.pos[3 * bid + 1], py, A.box[1], A.inv_box[1]);
+          const double dz = mi_comp(A.pos[3 * bid + 2], pz, A.box[2], A.inv_box[2]);
           geo[0] = (float)best;
           geo[1] = (float)__ddiv_rn(dx, best);
           geo[2] = (float)__ddiv_rn(dy, best);
@@ -169,25 +182,58 @@ __global__ void __launch_bounds__(256) features_kernel(FeatArgs A) {
 }
 
 // ---- network kernels --------------------------------------------------------------------
-// out[b][o] = act(sum_i in[b][i] W[o][i] + bias[o]), W and bias in BF16; z (pre-activation) optional.
-__global__ void dense_fwd_kernel(const float* __restrict__ in, int64_t B, int n, int o_dim,
-                                 const __nv_bfloat16* __restrict__ W, const __nv_bfloat16* __restrict__ bias,
-                                 float* __restrict__ z, float* __restrict__ out, int act) {
-  __shared__ float xs[16][kIn + 1];
-  const int64_t b0 = (int64_t)blockIdx.x * 16;
-  for (int i = threadIdx.x; i < 16 * n; i += blockDim.x) {
-    const int r = i / n, c = i % n;
-    xs[r][c] = (b0 + r < B) ? in[(b0 + r) * n + c] : 0.0f;
+// Y[b][o] = act(sum_k X[b][k] W[o][k] + bias[o]) (pre-activation into Z when given): a CTA computes
+// a 64-row x 64-output tile, each thread 4 x 4, with 32-wide k slices of X and W (W decoded from
+// BF16) staged in shared memory.
+template <int ACT>
+__global__ void __launch_bounds__(256) dense_fwd_tiled(const float* __restrict__ X, int64_t B, int n, int o_dim,
+                                                       const __nv_bfloat16* __restrict__ W,
+                                                       const __nv_bfloat16* __restrict__ bias, float* __restrict__ Z,
+                                                       float* __restrict__ Y) {
+  __shared__ float xs[32][68];
+  __shared__ float ws[32][68];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t r0 = (int64_t)blockIdx.x * 64;
+  const int o0 = blockIdx.y * 64;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    for (int i = threadIdx.x; i < 64 * 32; i += 256) {
+      const int r = i >> 5, k = i & 31;
+      xs[k][r] = (r0 + r < B && k0 + k < n) ? X[(r0 + r) * n + k0 + k] : 0.0f;
+      ws[k][r] = (o0 + r < o_dim && k0 + k < n) ? bf(W, (int64_t)(o0 + r) * n + k0 + k) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = xs[k][ty * 4 + i];
+        b[i] = ws[k][tx * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 16 * o_dim; i += blockDim.x) {
-    const int r = i / o_dim, o = i % o_dim;
-    if (b0 + r >= B) continue;
-    float acc = bf(bias, o);
-    const __nv_bfloat16* w = W + (int64_t)o * n;
-    for (int k = 0; k < n; ++k) acc += xs[r][k] * bf(w, k);
-    if (z) z[(b0 + r) * o_dim + o] = acc;
-    out[(b0 + r) * o_dim + o] = act ? silu_f(acc) : acc;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t r = r0 + ty * 4 + i;
+    if (r >= B) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int o = o0 + tx * 4 + j;
+      if (o >= o_dim) continue;
+      const float z = acc[i][j] + bf(bias, o);
+      if (Z) Z[r * o_dim + o] = z;
+      Y[r * o_dim + o] = ACT ? silu_f(z) : z;
+    }
   }
 }
 
@@ -301,10 +347,10 @@ namespace mka {
 mka_status mlp_forward_enqueue(const mka_mlp* net, const float* X, int64_t B, float* Z1, float* H1, float* Z2,
                                float* H2, float* Y, cudaStream_t st) {
   const __nv_bfloat16* P = net->thetab;
-  const unsigned nb = blocks_for(B, 16);
-  dense_fwd_kernel<<<nb, 256, 0, st>>>(X, B, kIn, kHid, P + oW1, P + ob1, Z1, H1, 1);
-  dense_fwd_kernel<<<nb, 256, 0, st>>>(H1, B, kHid, kHid, P + oW2, P + ob2, Z2, H2, 1);
-  dense_fwd_kernel<<<nb, 256, 0, st>>>(H2, B, kHid, kOut, P + oW3, P + ob3, nullptr, Y, 0);
+  const unsigned nb = blocks_for(B, 64);
+  dense_fwd_tiled<1><<<dim3(nb, 2), 256, 0, st>>>(X, B, kIn, kHid, P + oW1, P + ob1, Z1, H1);
+  dense_fwd_tiled<1><<<dim3(nb, 2), 256, 0, st>>>(H1, B, kHid, kHid, P + oW2, P + ob2, Z2, H2);
+  dense_fwd_tiled<0><<<dim3(nb, 2), 256, 0, st>>>(H2, B, kHid, kOut, P + oW3, P + ob3, nullptr, Y);
   count_launches(3);
   MKA_CUDA_TRY(cudaGetLastError());
   return MKA_OK;
@@ -314,8 +360,12 @@ mka_status features_enqueue(const mka_system* sys, const int64_t* d_sel, int64_t
                             cudaStream_t st) {
   FeatArgs A{};
   A.pos = sys->d_pos;
+  A.posf = sys->d_posf;
+  const double lmax = std::max(sys->box[0], std::max(sys->box[1], sys->box[2]));
+  A.pre_hi = (float)(1.0 + std::max(1e-3, 1e-5 * lmax / 5.5));
   for (int d = 0; d < 3; ++d) {
     A.box[d] = sys->box[d];
+    A.inv_box[d] = 1.0 / sys->box[d];
     A.ncell[d] = sys->cells.n[d];
     A.cell_len[d] = sys->cells.len[d];
   }

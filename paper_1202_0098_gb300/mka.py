@@ -186,13 +186,13 @@ def mka_system_info(sys) -> dict:
     return {"n_atoms": n.value, "nnzb": nnzb.value, "storage": st.value, "max_row_blocks": mrb.value}
 
 
-def mka_system_copy_bsr(sys) -> dict:
+def mka_system_copy_bsr(sys, values: bool = True) -> dict:
     info = mka_system_info(sys)
     n, nnzb = info["n_atoms"], info["nnzb"]
     row_ptr = np.empty(n + 1, np.int32)
     col = np.empty(nnzb, np.int32)
-    H = np.empty((nnzb, 4, 4))
-    S = np.empty((nnzb, 4, 4))
+    H = np.empty((nnzb, 4, 4)) if values else None
+    S = np.empty((nnzb, 4, 4)) if values else None
     _check(load().mka_system_copy_bsr(sys, _ptr(row_ptr), _ptr(col), _ptr(H), _ptr(S)), "mka_system_copy_bsr")
     return {"row_ptr": row_ptr, "col": col, "H": H, "S": S}
 

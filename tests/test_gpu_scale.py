@@ -1,0 +1,121 @@
+"""Parity at full size, in the launch configuration the benchmark times.
+
+The 10,077,696-atom system (BF16-stored H and S), one 65,536-atom batch through a plan
+(graph-replayed, as bench.py runs it): the mixed form against the FP64 form on every
+column of the batch (the FP64 form is itself held to 1e-10 against the oracle), and a
+few atoms of the batch against the oracle directly, both forms. The 10^6-atom
+amorphous-like system (sigma 0.15, R = 7 A, p = q = 20): 4,096 sampled columns
+(sample seed 33), mixed against FP64, and sampled atoms against the oracle.
+Bars: FP64 form |d rho| <= 1e-10; mixed |d rho| <= 1e-6, |d E| <= 1e-5 eV/atom.
+
+The mixed form needs its Krylov vectors as FP32 pairs to meet the bar at this size: s_j is
+nearly inside K_p(H; e_j) (the seam keeps about 1% of its S-norm), so a perturbation of the
+first chain at FP32 rounding level is magnified about 100-fold in the second chain's
+direction; a basis kept in plain FP32 gave max |d rho| 3.3e-6 on this batch.
+"""
+import numpy as np
+import pytest
+
+from oracle.parallel import solve_atoms_parallel
+from oracle import system as osys
+from synth import WORKLOADS, workload_positions, sample_atoms
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1202_0098_gb300 import build, mka
+    build.build()
+    mka.load()
+    return mka
+
+
+def plan_batch(mka, s, w, atoms, form):
+    prm = mka.solve_params(w.p, w.q, arith=form, cg_tol=1e-12 if form == "fp64" else 1e-7, keep_vectors=True)
+    plan = mka.mka_plan_create(s, len(atoms), prm)
+    mrb = mka.mka_system_info(s)["max_row_blocks"]
+    rho = torch.empty(len(atoms) * mrb * 16, dtype=torch.float64, device="cuda")
+    mka.mka_plan_run(plan, atoms, w.electrons_per_atom * len(atoms), w.kT, rho.data_ptr())
+    mu, e, n = mka.mka_plan_scalars(plan)
+    res = mka.mka_plan_result(plan)
+    lv = mka.mka_result_copy_levels(res)
+    nb = mka.mka_result_info(res)["n_blocks"]
+    return plan, res, lv, mu, e, rho[:nb * 16].cpu().numpy().reshape(nb, 4, 4)
+
+
+def test_full_size_batch_mixed_vs_fp64_and_oracle(lib):
+    mka = lib
+    w = WORKLOADS["diamond10m"]
+    pos, box = workload_positions(w)
+    s = mka.mka_build_system(pos, box, w.sk, "bf16", cluster_radius=w.R)
+    try:
+        B = 65536
+        atoms = np.arange(3 * B, 4 * B, dtype=np.int64)       # the bench's fourth batch
+        p64, r64, lv64, mu64, e64, rho64 = plan_batch(mka, s, w, atoms, "fp64")
+        p32, r32, lv32, mu32, e32, rho32 = plan_batch(mka, s, w, atoms, "mixed")
+        assert np.all(lv64["status"] == 0) and np.all(lv32["status"] == 0)
+        diff = np.abs(rho32 - rho64)
+        drho = diff.max()
+        print(f"10^7 batch of {B} atoms: mixed vs FP64 max|d rho| {drho:.2e}, |d E| {abs(e32 - e64) / B:.2e} eV/atom, "
+              f"|d mu| {abs(mu32 - mu64):.2e} eV")
+        print("  quantiles 0.5/0.99/0.9999/max:", np.quantile(diff, [0.5, 0.99, 0.9999, 1.0]),
+              "entries > 1e-6:", int((diff > 1e-6).sum()), "of", diff.size)
+        assert drho <= 1e-6 and abs(e32 - e64) / B <= 1e-5
+        # a few atoms of the batch against the oracle (same BF16-rounded values), rho at the FP64 form's mu
+        pick = np.array([0, 1, 4097, 30000, 65535])
+        ores = solve_atoms_parallel(pos, box, w.sk, w.R, atoms[pick], w.p, w.q, storage="bf16")
+        orho, _, _ = osys.density(ores, mu64, w.kT)
+        off = np.concatenate([[0], np.cumsum(np.diff(mka.mka_system_copy_bsr(s, values=False)["row_ptr"])[atoms])])
+        for k, t in enumerate(pick):
+            blk = slice(off[t], off[t + 1])
+            for res, tol in ((r64, 1e-10), (r32, 1e-6)):
+                rr = torch.empty(int(mka.mka_result_info(res)["n_blocks"]) * 16, dtype=torch.float64, device="cuda")
+                mka.mka_density_energy(s, res, mu64, w.kT, rr.data_ptr())
+                got = rr.cpu().numpy().reshape(-1, 4, 4)[blk]
+                assert np.abs(got - orho[k]).max() <= tol, (t, np.abs(got - orho[k]).max(), tol)
+        mka.mka_plan_destroy(p64)
+        mka.mka_plan_destroy(p32)
+    finally:
+        mka.mka_system_destroy(s)
+
+
+def test_amorphous_million_sampled_columns(lib):
+    mka = lib
+    w = WORKLOADS["diamond1m"]
+    pos, box = workload_positions(w)
+    s = mka.mka_build_system(pos, box, w.sk, "bf16", cluster_radius=w.R)
+    try:
+        atoms = sample_atoms(pos.shape[0], 1024, 33)            # 4,096 sampled columns
+        out = {}
+        for form in ("fp64", "mixed"):
+            prm = mka.solve_params(w.p, w.q, arith=form, cg_tol=1e-12 if form == "fp64" else 1e-7, keep_vectors=True)
+            res = mka.mka_solve_columns(s, atoms, prm)
+            lv = mka.mka_result_copy_levels(res)
+            mu = mka.mka_find_mu(res, w.electrons_per_atom * len(atoms), w.kT)
+            out[form] = (res, lv, mu)
+        mu = out["fp64"][2]
+        rhos = {}
+        for form in ("fp64", "mixed"):
+            res = out[form][0]
+            rr = torch.empty(int(mka.mka_result_info(res)["n_blocks"]) * 16, dtype=torch.float64, device="cuda")
+            e, _ = mka.mka_density_energy(s, res, mu, w.kT, rr.data_ptr())
+            rhos[form] = (rr.cpu().numpy().reshape(-1, 4, 4), e)
+        drho = np.abs(rhos["mixed"][0] - rhos["fp64"][0]).max()
+        de = abs(rhos["mixed"][1] - rhos["fp64"][1]) / len(atoms)
+        print(f"10^6 amorphous, 4096 columns: mixed vs FP64 max|d rho| {drho:.2e}, |d E| {de:.2e} eV/atom, "
+              f"|d mu| {abs(out['mixed'][2] - mu):.2e} eV")
+        assert drho <= 1e-6 and de <= 1e-5
+        pick = [0, 511, 1023]
+        ores = solve_atoms_parallel(pos, box, w.sk, w.R, atoms[pick], w.p, w.q, storage="bf16")
+        orho, _, _ = osys.density(ores, mu, w.kT)
+        off = np.concatenate([[0], np.cumsum(np.diff(mka.mka_system_copy_bsr(s, values=False)["row_ptr"])[atoms])])
+        for k, t in enumerate(pick):
+            blk = slice(off[t], off[t + 1])
+            assert np.abs(rhos["fp64"][0][blk] - orho[k]).max() <= 1e-10
+            assert np.abs(rhos["mixed"][0][blk] - orho[k]).max() <= 1e-6
+        for form in out:
+            mka.mka_result_destroy(out[form][0])
+    finally:
+        mka.mka_system_destroy(s)
