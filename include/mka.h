@@ -184,11 +184,13 @@ mka_status mka_solve_columns(mka_system* sys, const int64_t* atoms, int64_t n_se
  *               MKA_ERR_CLUSTER_TOO_LARGE when an atom's cluster has more
  *               than `max_cluster_atoms` atoms)
  * Pattern rows of v_alpha are not kept (no rho / G from this call).
- * Work memory (the work-queue counter, the atom list and one work slot per
- * CTA of 8 (3 (p+q) + 7) x 4 max_cluster_atoms x 4 bytes) comes from one
- * file-scope device array of MKA_STATIC_SCRATCH_BYTES. The call returns
- * MKA_ERR_INVALID_ARG, with a message, when the atom list and one slot do not
- * fit in it; fewer slots than SMs simply means fewer atoms in flight.
+ * Work memory (the work-queue counter, the atom list of a chunk, the chunk's
+ * reduced problems, 8 (2 nu^2 + 2 nu) bytes per column, and one work slot per
+ * CTA of about 8 (2 (p+q) + 2) x 4 max_cluster_atoms x 4 bytes) comes from one
+ * file-scope device array of MKA_STATIC_SCRATCH_BYTES; the selection runs in
+ * chunks sized to fit. The call returns MKA_ERR_INVALID_ARG, with a message,
+ * when one slot and one atom's reduced problems do not fit in it; fewer slots
+ * than SMs simply means fewer atoms in flight.
  * The call performs no cudaMalloc, cudaFree or other allocating routine. The
  * first call on a device looks up the array's device address (with that
  * device current) and caches it: make that first call before any stream
@@ -328,9 +330,11 @@ mka_status mka_plan_run(mka_plan* plan, const int64_t* atoms, int64_t n_sel, dou
  * last batch (host outputs, any may be NULL); synchronises the plan's stream. */
 mka_status mka_plan_scalars(mka_plan* plan, double* mu, double* e_band, double* n_elec);
 
-/* Device time (ms) of the per-atom kernel in the last batch, from events the
- * graph records around it; waits for that batch's kernel to finish. */
-mka_status mka_plan_kernel_ms(mka_plan* plan, float* ms);
+/* Device times (ms) of the last batch's two column kernels, from events the
+ * graph records around them: the per-atom kernel (cluster, CG, basis,
+ * projection) and the batched reduced problems (one lane per column). Either
+ * output may be NULL; waits for that batch's reduced problems to finish. */
+mka_status mka_plan_kernel_ms(mka_plan* plan, float* atoms_ms, float* reduced_ms);
 
 /* The plan's result object (levels, weights, status and kept rows of the last
  * batch), borrowed: valid until the next run or mka_plan_destroy, never

@@ -145,6 +145,7 @@ struct Args {
   // CG-only mode: stop after the inner CG and write s_j on the patch (training targets)
   int cg_only;
   float* cg_target;         // [4 n_sel][68]
+  double* red;              // reduced-problem buffer, lane-interleaved per 32 columns
 };
 
 // ---- small CTA helpers -------------------------------------------------------------
@@ -480,287 +481,15 @@ struct AtomState {
   int ncl, t0, flag, n_max, proj_any, acc_mask, act_mask;
 };
 
-// ---- warp-level FP64 reduced solve ------------------------------------------------------
-// Every function here is run by one whole warp on nv x nv matrices in shared memory
-// (row-major, leading dimension ld); lanes own rows or columns.
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// S = L L^T in place (lower triangle), rdiag[i] = 1 / L_ii. False when S is not positive definite.
-__device__ bool warp_cholesky(double* S, int n, int ld, double* rdiag) {
-  const int lane = threadIdx.x & 31;
-  for (int k = 0; k < n; ++k) {
-    const double d = S[k * ld + k];
-    __syncwarp();
-    if (!(d > 0.0)) return false;
-    const double lkk = sqrt(d), inv = 1.0 / lkk;
-    if (lane == 0) {
-      S[k * ld + k] = lkk;
-      rdiag[k] = inv;
-    }
-    for (int i = k + 1 + lane; i < n; i += 32) S[i * ld + k] *= inv;
-    __syncwarp();
-    for (int i = k + 1 + lane; i < n; i += 32) {
-      const double lik = S[i * ld + k];
-      for (int j = k + 1; j <= i; ++j) S[i * ld + j] -= lik * S[j * ld + k];
-    }
-    __syncwarp();
-  }
-  return true;
-}
-
-// H <- L^{-1} H L^{-T} for symmetric H (full storage), then symmetrised.
-__device__ void warp_congruence(double* H, const double* L, const double* rdiag, int n, int ld) {
-  const int lane = threadIdx.x & 31;
-  for (int j = lane; j < n; j += 32)          // X = L^{-1} H, column j by forward substitution
-    for (int i = 0; i < n; ++i) {
-      double v = H[i * ld + j];
-      for (int k = 0; k < i; ++k) v -= L[i * ld + k] * H[k * ld + j];
-      H[i * ld + j] = v * rdiag[i];
-    }
-  __syncwarp();
-  for (int i = lane; i < n; i += 32)          // A = X L^{-T}, row i by forward substitution
-    for (int j = 0; j < n; ++j) {
-      double v = H[i * ld + j];
-      for (int k = 0; k < j; ++k) v -= H[i * ld + k] * L[j * ld + k];
-      H[i * ld + j] = v * rdiag[j];
-    }
-  __syncwarp();
-  for (int i = lane; i < n; i += 32)
-    for (int j = 0; j < i; ++j) {
-      const double v = 0.5 * (H[i * ld + j] + H[j * ld + i]);
-      H[i * ld + j] = v;
-      H[j * ld + i] = v;
-    }
-  __syncwarp();
-}
-
-// Householder reduction of the symmetric A to tridiagonal form T = Q^T A Q: diagonal d,
-// off-diagonal e (e[k] couples k and k+1, e[n-1] = 0). On return A holds Q (accumulated in
-// place from the Householder vectors kept below the subdiagonal). p, tau: n doubles each.
-__device__ void warp_tridiag(double* A, int n, int ld, double* d, double* e, double* p, double* tau) {
-  const int lane = threadIdx.x & 31;
-  for (int k = 0; k + 2 < n; ++k) {
-    double s2 = 0.0;
-    for (int i = k + 1 + lane; i < n; i += 32) s2 += A[i * ld + k] * A[i * ld + k];
-    s2 = warp_sum_d(s2);
-    const double x0 = A[(k + 1) * ld + k];
-    const double nrm = sqrt(s2);
-    const double alpha = x0 >= 0.0 ? -nrm : nrm;
-    const double v0 = x0 - alpha;
-    const double vtv = s2 - x0 * x0 + v0 * v0;
-    const double tk = vtv > 0.0 ? 2.0 / vtv : 0.0;          // H_k = I - tk v v^T
-    __syncwarp();
-    if (lane == 0) {
-      A[(k + 1) * ld + k] = v0;                              // v = A[k+1.., k]
-      d[k] = A[k * ld + k];
-      e[k] = alpha;
-      tau[k] = tk;
-    }
-    __syncwarp();
-    for (int i = k + 1 + lane; i < n; i += 32) {             // p = tk B v
-      double acc = 0.0;
-      for (int j = k + 1; j < n; ++j) acc += A[i * ld + j] * A[j * ld + k];
-      p[i] = tk * acc;
-    }
-    __syncwarp();
-    double pv = 0.0;
-    for (int i = k + 1 + lane; i < n; i += 32) pv += p[i] * A[i * ld + k];
-    pv = warp_sum_d(pv);
-    const double kc = 0.5 * tk * pv;
-    __syncwarp();
-    for (int i = k + 1 + lane; i < n; i += 32) p[i] -= kc * A[i * ld + k];   // w = p - kc v
-    __syncwarp();
-    for (int i = k + 1 + lane; i < n; i += 32) {             // B -= v w^T + w v^T
-      const double vi = A[i * ld + k], wi = p[i];
-      for (int j = k + 1; j < n; ++j) A[i * ld + j] -= vi * p[j] + wi * A[j * ld + k];
-    }
-    __syncwarp();
-  }
-  if (lane == 0) {
-    if (n >= 2) {
-      d[n - 2] = A[(n - 2) * ld + (n - 2)];
-      e[n - 2] = A[(n - 1) * ld + (n - 2)];
-    }
-    d[n - 1] = A[(n - 1) * ld + (n - 1)];
-    e[n - 1] = 0.0;
-  }
-  __syncwarp();
-  // Q = H_0 H_1 ... H_{n-3}, accumulated backwards in place: before H_k is applied the
-  // trailing block [k+1.., k+1..] holds H_{k+1}...H_{n-3}; v_k sits in column k.
-  const int k0 = n >= 2 ? n - 2 : 0;
-  for (int i = k0 + lane; i < n; i += 32)
-    for (int j = k0; j < n; ++j) A[i * ld + j] = (i == j) ? 1.0 : 0.0;
-  __syncwarp();
-  for (int k = n - 3; k >= 0; --k) {
-    const int b = k + 1;
-    // grow the block by row/column b (identity there), keeping v_k in column k
-    for (int j = b + lane; j < n; j += 32) {
-      A[b * ld + j] = (j == b) ? 1.0 : 0.0;
-      A[j * ld + b] = (j == b) ? 1.0 : 0.0;
-    }
-    __syncwarp();
-    const double tk = tau[k];
-    if (tk != 0.0) {
-      for (int j = b + lane; j < n; j += 32) {               // p_j = tk sum_i v_i Q_ij
-        double y = 0.0;
-        for (int i = b; i < n; ++i) y += A[i * ld + k] * A[i * ld + j];
-        p[j] = tk * y;
-      }
-      __syncwarp();
-      for (int i = b + lane; i < n; i += 32) {
-        const double vi = A[i * ld + k];
-        for (int j = b; j < n; ++j) A[i * ld + j] -= vi * p[j];
-      }
-      __syncwarp();
-    }
-  }
-  for (int j = lane; j < n; j += 32) {                       // row / column 0 of Q
-    A[j] = (j == 0) ? 1.0 : 0.0;
-    A[j * ld] = (j == 0) ? 1.0 : 0.0;
-  }
-  __syncwarp();
-}
-
-// Eigenvalues of the symmetric tridiagonal (d, e) by the implicit-shift QL method
-// (Bowdler, Martin, Reinsch & Wilkinson, Numer. Math. 11, 1968), with every rotation also
-// applied to the columns of Z. Lane 0 runs the scalar recurrence of one sweep and records
-// its rotations (rc, rs); then every lane applies them to its rows of Z in order.
-// Returns false when an eigenvalue needs more than 60 sweeps.
-__device__ bool warp_tql(double* d, double* e, double* Z, int n, int ld, double* rc, double* rs, int* ctl) {
-  const int lane = threadIdx.x & 31;
-  for (int l = 0; l < n; ++l) {
-    for (int iter = 0;; ++iter) {
-      // ctl[0] = m (end of the unreduced block), ctl[1] = first recorded rotation index, ctl[2] = status
-      if (lane == 0) {
-        int m = l;
-        for (; m < n - 1; ++m) {
-          const double dd = fabs(d[m]) + fabs(d[m + 1]);
-          if (fabs(e[m]) <= 2.2204460492503131e-16 * dd) break;
-        }
-        ctl[0] = m;
-        ctl[1] = m;          // no rotation recorded yet
-        ctl[2] = 0;
-        if (m != l) {
-          if (iter == 60) {
-            ctl[2] = 1;
-          } else {
-            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = sqrt(g * g + 1.0);
-            g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
-            double s = 1.0, c = 1.0, p = 0.0;
-            bool early = false;
-            int i = m - 1;
-            for (; i >= l; --i) {
-              const double f = s * e[i], b = c * e[i];
-              r = sqrt(f * f + g * g);
-              e[i + 1] = r;
-              if (r == 0.0) {
-                d[i + 1] -= p;
-                e[m] = 0.0;
-                early = true;
-                break;
-              }
-              const double rinv = 1.0 / r;
-              s = f * rinv;
-              c = g * rinv;
-              g = d[i + 1] - p;
-              r = (d[i] - g) * s + 2.0 * c * b;
-              p = s * r;
-              d[i + 1] = g + p;
-              g = c * r - b;
-              rc[i] = c;
-              rs[i] = s;
-            }
-            ctl[1] = early ? i + 1 : l;
-            if (!early) {
-              d[l] -= p;
-              e[l] = g;
-              e[m] = 0.0;
-            }
-          }
-        }
-      }
-      __syncwarp();
-      const int m = ctl[0], i0 = ctl[1];
-      if (ctl[2]) return false;
-      if (m == l) break;
-      if (Z) {
-        for (int k = lane; k < n; k += 32) {
-          for (int i = m - 1; i >= i0; --i) {
-            const double c = rc[i], s = rs[i];
-            const double f = Z[k * ld + i + 1];
-            Z[k * ld + i + 1] = s * Z[k * ld + i] + c * f;
-            Z[k * ld + i] = c * Z[k * ld + i] - s * f;
-          }
-        }
-      }
-      __syncwarp();
-    }
-  }
-  return true;
-}
-
-// Per-warp scratch of the reduced solve (doubles): rdiag, e, p, tau, rc, rs (n each),
-// 4 control ints, the ranks (n ints) and the eigenvalues (n).
-__host__ __device__ constexpr size_t red_scratch_doubles(int nu) { return (size_t)6 * nu + 2 + (nu + 1) / 2 + nu; }
-
-struct RedScratch {
-  double *rdiag, *e, *p, *tau, *rc, *rs, *evals;
-  int *ctl, *rank;
-  __device__ RedScratch(double* w, int nu) {
-    rdiag = w;
-    e = w + nu;
-    p = w + 2 * nu;
-    tau = w + 3 * nu;
-    rc = w + 4 * nu;
-    rs = w + 5 * nu;
-    ctl = reinterpret_cast<int*>(w + 6 * nu);
-    rank = reinterpret_cast<int*>(w + 6 * nu + 2);
-    evals = w + 6 * nu + 2 + (nu + 1) / 2;
-  }
-};
-
-// Reduced problem of one column (Eq. EQ-SUB-EIG-VEC with S_r formed explicitly): Cholesky of S_r
-// (in Lm), A = L^{-1} H_r L^{-T}, tridiagonalisation, QL; on return Hm holds C = L^{-T} Q Z
-// (column a = eigenvector a, unsorted), evals[a] its eigenvalue and rank[a] its ascending
-// position. False when S_r is not positive definite or QL fails.
-__device__ bool warp_reduced_solve(double* Hm, double* Lm, int n, int ld, const RedScratch& w) {
-  const int lane = threadIdx.x & 31;
-  if (!warp_cholesky(Lm, n, ld, w.rdiag)) return false;
-  warp_congruence(Hm, Lm, w.rdiag, n, ld);
-  warp_tridiag(Hm, n, ld, w.evals, w.e, w.p, w.tau);
-  if (!warp_tql(w.evals, w.e, Hm, n, ld, w.rc, w.rs, w.ctl)) return false;
-  for (int a = lane; a < n; a += 32)            // C = L^{-T} Z, column a by back substitution, in place
-    for (int i = n - 1; i >= 0; --i) {
-      double v = Hm[i * ld + a];
-      for (int k = i + 1; k < n; ++k) v -= Lm[k * ld + i] * Hm[k * ld + a];
-      Hm[i * ld + a] = v * w.rdiag[i];
-    }
-  for (int a = lane; a < n; a += 32) {
-    const double ea = w.evals[a];
-    int r = 0;
-    for (int k = 0; k < n; ++k) {
-      const double f = w.evals[k];
-      r += (f < ea) || (f == ea && k < a);
-    }
-    w.rank[a] = r;
-  }
-  __syncwarp();
-  return true;
-}
-
 // One Gram-Schmidt coefficient sweep over u_0..u_{nmax-1} (one warp per vector, lanes over
 // rows): coef[mm][c] = (S u_mm)^T l for columns whose basis holds mm (when do_coef), and, for
 // columns with a pending projection column pn = n - 1, H_r[mm][pn] = u_mm^T (H u_pn) and
-// S_r[mm][pn] = u_mm^T (S u_pn) written (with their mirror) to HS.
+// S_r[mm][pn] = u_mm^T (S u_pn) written (with their mirror) to the reduced-problem buffer of
+// column col0 + c.
 template <typename T>
 __device__ void gs_sweep(const T* U, const T* SU, const T* L, const T* KV, const T* SV, int m, int m_cap, int nmax,
-                         bool do_coef, const AtomState& st, double* coef, T* coefT, double* HS, int nu) {
+                         bool do_coef, const AtomState& st, double* coef, T* coefT, double* red, int64_t col0,
+                         int nu) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const bool proj = st.proj_any;
   for (int mm = wid; mm < nmax; mm += (int)(blockDim.x >> 5)) {
@@ -798,12 +527,13 @@ __device__ void gs_sweep(const T* U, const T* SU, const T* L, const T* KV, const
       }
       if (proj && st.proj[c] && mm < st.n[c]) {
         const int pn = st.n[c] - 1;
-        double* H = HS + (size_t)c * 2 * nu * nu;
-        double* S = H + (size_t)nu * nu;
-        H[mm * nu + pn] = (double)ph[c];
-        H[pn * nu + mm] = (double)ph[c];
-        S[mm * nu + pn] = (double)ps[c];
-        S[pn * nu + mm] = (double)ps[c];
+        const int64_t col = col0 + c;
+        double* H = red + (size_t)(col >> 5) * red_block_doubles(nu) * 32 + (col & 31);
+        double* S = H + (size_t)nu * nu * 32;
+        H[(size_t)(mm * nu + pn) * 32] = (double)ph[c];
+        H[(size_t)(pn * nu + mm) * 32] = (double)ph[c];
+        S[(size_t)(mm * nu + pn) * 32] = (double)ps[c];
+        S[(size_t)(pn * nu + mm) * 32] = (double)ps[c];
       }
     }
   }
@@ -823,7 +553,6 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
   __shared__ int cnt;
 
   const int nu = A.nu;
-  const int ld = nu + 1;
   const int m_cap = A.mcap;
   int* cl = reinterpret_cast<int*>(smem_raw);                            // kMaxCl
   int* lrow = cl + kMaxCl;                                                // kMaxCl + 1
@@ -831,22 +560,19 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
   uint16_t* lcol = reinterpret_cast<uint16_t*>(lblk + A.lnnz_cap);        // lnnz_cap
   size_t off = (size_t)(2 * kMaxCl + 1 + A.lnnz_cap) * sizeof(int) + (size_t)A.lnnz_cap * sizeof(uint16_t);
   off = (off + 15) & ~(size_t)15;
-  unsigned char* region = smem_raw + off;   // work vectors during CG and basis; reduced matrices afterwards
+  unsigned char* region = smem_raw + off;   // work vectors of CG and the basis
   T* V0 = reinterpret_cast<T*>(region);     // CG: p     basis: l
   T* V1 = V0 + (size_t)m_cap * 4;           // CG: S p   basis: S l, then S u_{n-1}
   T* V2 = V1 + (size_t)m_cap * 4;           // CG: r     basis: H u_{n-1}
   // FP32 form only: the low halves of l and H u_{n-1}
   float* Llo = reinterpret_cast<float*>(V2 + (size_t)m_cap * 4);
   float* Klo = Llo + (size_t)m_cap * 4;
-  double* RM = reinterpret_cast<double*>(region);   // per column: H_r / C (nu x ld), S_r / L, 8 nu scratch
-  const size_t rm_col = (size_t)2 * nu * ld + red_scratch_doubles(nu);
 
   char* slot = A.scratch + (size_t)blockIdx.x * A.slot_bytes;
   T* U = reinterpret_cast<T*>(slot);                 // [nu][m_cap][4]
   T* SU = U + (size_t)nu * m_cap * 4;                // [nu][m_cap][4]
   T* SJ = SU + (size_t)nu * m_cap * 4;               // s_j, [m_cap][4]
-  double* HS = reinterpret_cast<double*>(slot + align_up(sizeof(T) * ((size_t)2 * nu + 1) * m_cap * 4, 256));
-  double* SJd = reinterpret_cast<double*>(reinterpret_cast<char*>(HS) + align_up(sizeof(double) * 8 * (size_t)nu * nu, 256));
+  double* SJd = reinterpret_cast<double*>(slot + align_up(sizeof(T) * ((size_t)2 * nu + 1) * m_cap * 4, 256));
   (void)SJd;   // FP32 arithmetic only: s_j in FP64 for the seam [m_cap][4]
   // FP32 arithmetic only: low halves of the basis vectors [nu][m_cap][4]
   float* Ulo = reinterpret_cast<float*>(reinterpret_cast<char*>(SJd) + align_up(sizeof(double) * 4 * (size_t)m_cap, 256));
@@ -867,15 +593,11 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
     // ---- 1. cluster ----------------------------------------------------------------
     const int ncl_raw = gather_cluster(A, atom, cl, &cnt);
     if (ncl_raw > kMaxCl || 4 * ncl_raw > m_cap) {
-      for (int c = threadIdx.x; c < 4; c += blockDim.x) {
+      for (int c = threadIdx.x; c < 4; c += blockDim.x) {   // the reduced pass writes zero outputs
         const int64_t col = 4 * widx + c;
         A.status[col] = ST_TOOLARGE;
         A.nu_eff[col] = 0;
         A.cg_iters[col] = 0;
-      }
-      for (int i = threadIdx.x; i < 4 * nu; i += blockDim.x) {
-        A.eps[4 * widx * nu + i] = 0.0;
-        A.w[4 * widx * nu + i] = 0.0;
       }
       __syncthreads();
       continue;
@@ -898,7 +620,11 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
     }
     __syncthreads();
     if (!st.flag) {  // cannot happen with a capacity of (largest cluster) x (longest row)
-      for (int c = threadIdx.x; c < 4; c += blockDim.x) A.status[4 * widx + c] = ST_TOOLARGE;
+      for (int c = threadIdx.x; c < 4; c += blockDim.x) {
+        A.status[4 * widx + c] = ST_TOOLARGE;
+        A.nu_eff[4 * widx + c] = 0;
+        A.cg_iters[4 * widx + c] = 0;
+      }
       __syncthreads();
       continue;
     }
@@ -1125,7 +851,7 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
       __syncthreads();
       const int nmax = st.n_max;
       for (int pass = 0; pass < 2 && nmax > 0; ++pass) {
-        gs_sweep<T>(U, SU, Lv, KV, SL, m, m_cap, nmax, true, st, coef, coefT, HS, nu);
+        gs_sweep<T>(U, SU, Lv, KV, SL, m, m_cap, nmax, true, st, coef, coefT, A.red, 4 * widx, nu);
         if (threadIdx.x < 4) {
           double s = 0;
           for (int mm = 0; mm < nmax; ++mm) s += coef[mm * 4 + threadIdx.x] * coef[mm * 4 + threadIdx.x];
@@ -1320,109 +1046,43 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
         st.n_max = nm;
       }
       __syncthreads();
-      gs_sweep<T>(U, SU, Lv, KV, SL, m, m_cap, st.n_max, false, st, coef, coefT, HS, nu);
+      gs_sweep<T>(U, SU, Lv, KV, SL, m, m_cap, st.n_max, false, st, coef, coefT, A.red, 4 * widx, nu);
     }
 
-    // ---- 4./5. reduced problems (one warp per column) and outputs ----------------------
-    // H_r, S_r into shared memory (the work vectors are no longer needed)
-    for (int c = 0; c < 4; ++c) {
-      const int nv = st.n[c];
-      double* Hm = RM + (size_t)c * rm_col;
-      double* Lm = Hm + (size_t)nu * ld;
-      const double* H = HS + (size_t)c * 2 * nu * nu;
-      const double* S = H + (size_t)nu * nu;
-      for (int i = threadIdx.x; i < nv * nv; i += blockDim.x) {
-        const int a = i / nv, b = i % nv;
-        Hm[a * ld + b] = H[a * nu + b];
-        Lm[a * ld + b] = S[a * nu + b];
+    // ---- 4. what the reduced problems need: row j of U and S U (H_r, S_r are in place) -------
+    {
+      double* red0 = A.red + (size_t)((4 * widx) >> 5) * red_block_doubles(nu) * 32;
+      for (int i = threadIdx.x; i < 4 * 2 * nu; i += blockDim.x) {
+        const int c = i / (2 * nu), k = i % (2 * nu), n = k % nu;
+        const int64_t col = 4 * widx + c;
+        if (n >= st.n[c]) continue;
+        const T* src = (k < nu ? U : SU) + (size_t)n * m_cap * 4 + 4 * (4 * t0 + c) + c;
+        red0[((size_t)2 * nu * nu + k) * 32 + (col & 31)] = (double)*src;
       }
     }
-    __syncthreads();
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (wid < 4) {
-      const int c = wid;
+    for (int c = threadIdx.x; c < 4; c += blockDim.x) {
       const int64_t col = 4 * widx + c;
-      const int nv = st.n[c];
-      double* Hm = RM + (size_t)c * rm_col;
-      double* Lm = Hm + (size_t)nu * ld;
-      const RedScratch wsc(Lm + (size_t)nu * ld, nu);
-      int stc = st.status[c];
-      if (stc == ST_OK && nv < nu) stc = ST_BREAKDOWN;
-      bool ok = (st.status[c] == ST_OK) && nv > 0;
-      if (ok) ok = warp_reduced_solve(Hm, Lm, nv, ld, wsc);
-      if (!ok && st.status[c] == ST_OK) stc = ST_NOT_SPD;
-      if (lane == 0) {
-        A.status[col] = stc;
-        A.nu_eff[col] = ok ? nv : 0;
-        A.cg_iters[col] = st.it[c];
-        st.accept[c] = ok;    // reused as "reduced solve succeeded"
-      }
-    }
-    __syncthreads();
-    // C in the arithmetic type, once per column, into the (now free) L region
-    for (int i = threadIdx.x; i < 4 * nu * nu; i += blockDim.x) {
-      const int c = i / (nu * nu), n = (i / nu) % nu, a = i % nu;
-      if (!st.accept[c] || n >= st.n[c] || a >= st.n[c]) continue;
-      const double* Hm = RM + (size_t)c * rm_col;
-      T* CT = reinterpret_cast<T*>(const_cast<double*>(Hm) + (size_t)nu * ld);
-      CT[n * ld + a] = (T)Hm[n * ld + a];
-    }
-    // ---- outputs of the four columns, all threads -----------------------------------------
-    const int e0 = lrow[t0], e1 = lrow[t0 + 1];
-    const int64_t rbase = A.row_ptr[atom];
-    const int nrow = A.row_ptr[atom + 1] - A.row_ptr[atom];
-    for (int i = threadIdx.x; i < 4 * nu; i += blockDim.x) {
-      A.eps[4 * widx * nu + i] = 0.0;
-      A.w[4 * widx * nu + i] = 0.0;
-    }
-    if (A.keep)
-      for (int i = threadIdx.x; i < nrow * 16 * nu; i += blockDim.x) A.vp[A.blk_off[widx] * 16 * nu + i] = 0.0;
-    __syncthreads();
-    // eps_alpha and w_alpha = V_{j alpha} (S V)_{j alpha}: thread per (column, alpha)
-    for (int i = threadIdx.x; i < 4 * nu; i += blockDim.x) {
-      const int c = i / nu, a = i % nu, nv = st.n[c];
-      if (!st.accept[c] || a >= nv) continue;
-      const double* Hm = RM + (size_t)c * rm_col;
-      const RedScratch wsc(const_cast<double*>(Hm) + (size_t)2 * nu * ld, nu);
-      const int jr = 4 * t0 + c;
-      const T* CT = reinterpret_cast<const T*>(Hm + (size_t)nu * ld);
-      T vj = 0, svj = 0;
-      for (int n = 0; n < nv; ++n) {
-        const T cn = CT[n * ld + a];
-        vj += U[(size_t)n * m_cap * 4 + 4 * jr + c] * cn;
-        svj += SU[(size_t)n * m_cap * 4 + 4 * jr + c] * cn;
-      }
-      const int ra = wsc.rank[a];
-      A.eps[(4 * widx + c) * nu + ra] = wsc.evals[a];
-      A.w[(4 * widx + c) * nu + ra] = (double)vj * (double)svj;
+      A.status[col] = st.status[c];
+      A.nu_eff[col] = st.n[c];
+      A.cg_iters[col] = st.it[c];
     }
     if (A.keep) {
-      // pattern rows of V = U C: thread per (column, pattern block, orbital row), alpha in chunks of 8
-      const int ne = e1 - e0;
-      for (int i = threadIdx.x; i < 16 * ne; i += blockDim.x) {
-        const int c = i / (4 * ne), rem = i % (4 * ne), e = e0 + rem / 4, r = rem % 4, nv = st.n[c];
-        if (!st.accept[c]) continue;
-        const double* Hm = RM + (size_t)c * rm_col;
-        const RedScratch wsc(const_cast<double*>(Hm) + (size_t)2 * nu * ld, nu);
+      // pattern rows of U (zero outside the cluster); the reduced pass turns them into rows of V = U C
+      const int64_t rbase = A.row_ptr[atom];
+      const int nrow = A.row_ptr[atom + 1] - A.row_ptr[atom];
+      double* vpa = A.vp + A.blk_off[widx] * 16 * (int64_t)nu;
+      for (int i = threadIdx.x; i < nrow * 16 * nu; i += blockDim.x) vpa[i] = 0.0;
+      __syncthreads();
+      const int e0 = lrow[t0], ne = lrow[t0 + 1] - e0;
+      for (int i = threadIdx.x; i < 16 * ne * nu; i += blockDim.x) {
+        const int n = i % nu, rem = i / nu, c = rem / (4 * ne), er = rem % (4 * ne), e = e0 + er / 4, r = er % 4;
+        if (n >= st.n[c]) continue;
         const int k = (int)(lblk[e] - rbase);
-        const T* urow = U + 4 * (4 * (int)lcol[e] + r) + c;
-        const T* CT = reinterpret_cast<const T*>(Hm + (size_t)nu * ld);
-        double* out = A.vp + ((A.blk_off[widx] + k) * 16 + c * 4 + r) * (int64_t)nu;
-        for (int a0 = 0; a0 < nv; a0 += 8) {
-          T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-          for (int n = 0; n < nv; ++n) {
-            const T un = urow[(size_t)n * m_cap * 4];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[j] += un * (a0 + j < nv ? CT[n * ld + a0 + j] : (T)0);
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (a0 + j < nv) out[wsc.rank[a0 + j]] = (double)acc[j];
-        }
+        vpa[((int64_t)k * 16 + c * 4 + r) * nu + n] = (double)U[(size_t)n * m_cap * 4 + 4 * (4 * (int)lcol[e] + r) + c];
       }
       if (threadIdx.x == 0) {
         int sk = -1;
-        for (int e = e0; e < e1; ++e)
+        for (int e = e0; e < e0 + ne; ++e)
           if (lcol[e] == t0) sk = (int)(lblk[e] - rbase);
         A.self_k[widx] = sk;
       }
@@ -1480,24 +1140,20 @@ void fill_system_args(Args<TV>& A, const mka_system* s) {
   A.cell_atoms = s->cells.atoms;
 }
 
-// Dynamic shared memory of atoms_kernel: cluster list and local pattern, then one region that
-// holds three [m_cap][4] work vectors during CG and the basis, and the four columns' reduced
-// matrices (H_r / C, S_r / L and scratch) afterwards.
-size_t dyn_smem_bytes(int nu, int lnnz_cap, int mcap, size_t elem) {
+// Dynamic shared memory of atoms_kernel: cluster list and local pattern, then the [m_cap][4]
+// work vectors of CG and the basis (three, and two low halves in the FP32 form).
+size_t dyn_smem_bytes(int lnnz_cap, int mcap, size_t elem) {
   size_t off = (size_t)(2 * kMaxCl + 1 + lnnz_cap) * sizeof(int) + (size_t)lnnz_cap * sizeof(uint16_t);
   off = align_up(off, 16);
-  const int ld = nu + 1;
-  const size_t vec = (size_t)(elem == 4 ? 5 : 3) * mcap * 4 * elem;
-  const size_t red = sizeof(double) * 4 * ((size_t)2 * nu * ld + red_scratch_doubles(nu));
-  return off + std::max(vec, red);
+  return off + (size_t)(elem == 4 ? 5 : 3) * mcap * 4 * elem;
 }
 
 // Per-CTA global work slot: U and S U ([nu][m_cap][4]) and s_j ([m_cap][4]) in the arithmetic
-// type, then H_r and S_r of the four columns (FP64, nu x nu each), then s_j in FP64 ([m_cap][4]),
-// then (FP32 arithmetic) the low halves of the basis vectors ([nu][m_cap][4] FP32).
+// type, then s_j in FP64 ([m_cap][4]), then (FP32 arithmetic) the low halves of the basis
+// vectors ([nu][m_cap][4] FP32).
 size_t slot_bytes_for(int nu, int mcap, size_t elem) {
-  return align_up(elem * ((size_t)2 * nu + 1) * mcap * 4, 256) + align_up(sizeof(double) * 8 * (size_t)nu * nu, 256) +
-         align_up(sizeof(double) * 4 * (size_t)mcap, 256) + (elem == 4 ? align_up(4 * (size_t)nu * mcap * 4, 256) : 0);
+  return align_up(elem * ((size_t)2 * nu + 1) * mcap * 4, 256) + align_up(sizeof(double) * 4 * (size_t)mcap, 256) +
+         (elem == 4 ? align_up(4 * (size_t)nu * mcap * 4, 256) : 0);
 }
 
 template <typename TV, typename T, int NT>
@@ -1506,7 +1162,7 @@ mka_status config_t(const mka_system* sys, int nu, int max_cl, int ctas_per_sm, 
   cf.threads = NT;
   cf.mcap = 4 * std::max(1, std::min(max_cl, kMaxCl));
   cf.lnnz_cap = std::max(1, std::min(max_cl, kMaxCl) * std::max(1, sys->max_row_blocks));
-  cf.smem = dyn_smem_bytes(nu, cf.lnnz_cap, cf.mcap, sizeof(T));
+  cf.smem = dyn_smem_bytes(cf.lnnz_cap, cf.mcap, sizeof(T));
   cf.slot_bytes = slot_bytes_for(nu, cf.mcap, sizeof(T));
   auto kern = atoms_kernel<TV, T, NT>;
   MKA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem));
@@ -1554,6 +1210,8 @@ mka_status launch_t(const mka_system* sys, const AtomsConfig& cf, const AtomsLau
   A.fallback = a.fallback;
   A.cg_only = a.cg_only;
   A.cg_target = a.cg_target;
+  A.red = a.red;
+  if (!a.cg_only && !a.red) return fail(MKA_ERR_INVALID_ARG, "the per-atom kernel needs a reduced-problem buffer");
   atoms_kernel<TV, T, NT><<<(unsigned)a.grid, NT, cf.smem, st>>>(A);
   count_launches();
   MKA_CUDA_TRY(cudaGetLastError());
@@ -1595,6 +1253,11 @@ mka_status atoms_config(const mka_system* sys, int nu, int arith, int max_cl, in
 #undef MKA_CFG
 }
 
+mka_status reduced_for(const mka_system* sys, const AtomsLaunchArgs& a, cudaStream_t st) {
+  return reduced_launch(a.red, 4 * a.n_sel, a.p + a.q, a.status, a.nu_eff, a.eps, a.w, a.keep, a.vp, a.blk_off, a.sel,
+                        sys->d_row_ptr, st);
+}
+
 mka_status atoms_launch(const mka_system* sys, int arith, const AtomsConfig& cf, const AtomsLaunchArgs& a,
                         cudaStream_t st) {
   const bool mixed = arith != MKA_FP64;
@@ -1605,55 +1268,70 @@ mka_status atoms_launch(const mka_system* sys, int arith, const AtomsConfig& cf,
 
 mka_status launch_columns(mka_system* sys, mka_result* res, const mka_solve_params* prm, int max_cl,
                           cudaStream_t st) {
+  const int nu = prm->p + prm->q;
   AtomsConfig cf{};
-  mka_status s = atoms_config(sys, prm->p + prm->q, prm->arith, max_cl, 256, 0, &cf);
+  mka_status s = atoms_config(sys, nu, prm->arith, max_cl, 256, 0, &cf);
   if (s) return s;
-  const int64_t grid = std::min<int64_t>(res->n_sel, cf.grid_max);
+  // atoms per chunk: the reduced-problem buffer of a chunk stays within 2 GiB
+  const size_t per_atom = red_buffer_bytes(32, nu) / 8;
+  const int64_t chunk = std::max<int64_t>(8, std::min<int64_t>(res->n_sel, ((size_t)2 << 30) / per_atom) & ~(int64_t)7);
+  const int64_t grid = std::min<int64_t>(std::min(res->n_sel, chunk), cf.grid_max);
   char* scratch = nullptr;
   int* counter = nullptr;
+  double* red = nullptr;
   MKA_CUDA_TRY(cudaMallocAsync(&scratch, cf.slot_bytes * grid + 256, st));
   MKA_CUDA_TRY(cudaMallocAsync(&counter, sizeof(int), st));
-  MKA_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
-  AtomsLaunchArgs a{};
-  // learned warm start: features, then the network's prediction of s_j on each patch
+  MKA_CUDA_TRY(cudaMallocAsync(&red, red_buffer_bytes(4 * std::min(res->n_sel, chunk), nu), st));
+  // learned warm start: features, then the network's prediction of s_j on each patch (per chunk)
   float* wbuf = nullptr;
   int32_t* patch = nullptr;
+  const int64_t rows_max = 4 * std::min(res->n_sel, chunk);
   if (prm->use_warm_start) {
-    const int64_t rows = 4 * res->n_sel;
-    MKA_CUDA_TRY(cudaMallocAsync(&wbuf, sizeof(float) * (rows * (132 + 68) + mlp_work_floats(rows)), st));
-    MKA_CUDA_TRY(cudaMallocAsync(&patch, sizeof(int32_t) * 17 * res->n_sel, st));
-    float* X = wbuf;
-    float* Y = X + rows * 132;
-    float* W = Y + rows * 68;
-    s = features_enqueue(sys, res->d_sel, res->n_sel, X, patch, st);
-    if (!s) s = mlp_forward_enqueue(sys->warm, X, rows, W, W + rows * 128, W + 2 * rows * 128, W + 3 * rows * 128, Y, st);
-    if (s) return s;
-    a.x0 = Y;
-    a.patch = patch;
-    a.fallback = res->d_fallback;
+    MKA_CUDA_TRY(cudaMallocAsync(&wbuf, sizeof(float) * (rows_max * (132 + 68) + mlp_work_floats(rows_max)), st));
+    MKA_CUDA_TRY(cudaMallocAsync(&patch, sizeof(int32_t) * 17 * std::min(res->n_sel, chunk), st));
   }
-  a.sel = res->d_sel;
-  a.order = nullptr;
-  a.n_sel = res->n_sel;
-  a.p = prm->p;
-  a.q = prm->q;
-  a.cg_tol = prm->cg_tol;
-  a.cg_maxit = prm->cg_maxit;
-  a.eps = res->d_eps;
-  a.w = res->d_w;
-  a.nu_eff = res->d_nu_eff;
-  a.cg_iters = res->d_cg_iters;
-  a.status = res->d_status;
-  a.keep = res->keep;
-  a.vp = res->d_vp;
-  a.blk_off = res->d_blk_off;
-  a.self_k = res->d_self;
-  a.scratch = scratch;
-  a.counter = counter;
-  a.grid = (int)grid;
-  s = atoms_launch(sys, prm->arith, cf, a, st);
+  for (int64_t off = 0; off < res->n_sel && !s; off += chunk) {
+    const int64_t cnt = std::min(chunk, res->n_sel - off);
+    AtomsLaunchArgs a{};
+    if (prm->use_warm_start) {
+      const int64_t rows = 4 * cnt;
+      float* X = wbuf;
+      float* Y = X + rows * 132;
+      float* W = Y + rows * 68;
+      s = features_enqueue(sys, res->d_sel + off, cnt, X, patch, st);
+      if (!s) s = mlp_forward_enqueue(sys->warm, X, rows, W, W + rows * 128, W + 2 * rows * 128, W + 3 * rows * 128, Y, st);
+      if (s) break;
+      a.x0 = Y;
+      a.patch = patch;
+      a.fallback = res->d_fallback + 4 * off;
+    }
+    MKA_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    a.sel = res->d_sel + off;
+    a.order = nullptr;
+    a.n_sel = cnt;
+    a.p = prm->p;
+    a.q = prm->q;
+    a.cg_tol = prm->cg_tol;
+    a.cg_maxit = prm->cg_maxit;
+    a.eps = res->d_eps + 4 * off * nu;
+    a.w = res->d_w + 4 * off * nu;
+    a.nu_eff = res->d_nu_eff + 4 * off;
+    a.cg_iters = res->d_cg_iters + 4 * off;
+    a.status = res->d_status + 4 * off;
+    a.keep = res->keep;
+    a.vp = res->d_vp;
+    a.blk_off = res->keep ? res->d_blk_off + off : nullptr;
+    a.self_k = res->keep ? res->d_self + off : nullptr;
+    a.scratch = scratch;
+    a.counter = counter;
+    a.red = red;
+    a.grid = (int)std::min<int64_t>(grid, cnt);
+    s = atoms_launch(sys, prm->arith, cf, a, st);
+    if (!s) s = reduced_for(sys, a, st);
+  }
   cudaFreeAsync(scratch, st);
   cudaFreeAsync(counter, st);
+  cudaFreeAsync(red, st);
   if (wbuf) cudaFreeAsync(wbuf, st);
   if (patch) cudaFreeAsync(patch, st);
   return s;
@@ -1702,39 +1380,51 @@ mka_status run_columns_static(const mka_system* sys, const int64_t* h_atoms, int
   AtomsConfig cf{};
   s = atoms_config(sys, p + q, MKA_FP64, max_cl, 256, 0, &cf);
   if (s) return s;
-  // layout: [work counter | 256 B] [atom ids | rounded to 256 B] [per-CTA slots]
-  const size_t sel_bytes = align_up((size_t)n_sel * sizeof(int64_t), 256);
-  const size_t fixed = 256 + sel_bytes;
-  if (fixed + cf.slot_bytes > (size_t)MKA_STATIC_SCRATCH_BYTES)
+  // layout: [work counter | 256 B] [atom ids of a chunk | rounded to 256 B] [reduced-problem buffer of
+  // the chunk] [per-CTA slots]; the selection runs in chunks that leave room for at least one slot
+  const int nu = p + q;
+  const size_t total = (size_t)MKA_STATIC_SCRATCH_BYTES;
+  const size_t per_atom = sizeof(int64_t) + red_buffer_bytes(32, nu) / 8;
+  if (256 + cf.slot_bytes + 256 + red_buffer_bytes(4, nu) > total)
     return fail(MKA_ERR_INVALID_ARG,
-                "mka_solve_columns_static: one work slot (" + std::to_string(cf.slot_bytes) + " B) plus the atom list (" +
-                    std::to_string(sel_bytes) + " B) exceeds the fixed scratch of " +
-                    std::to_string((size_t)MKA_STATIC_SCRATCH_BYTES) +
-                    " B; pass fewer atoms, a smaller p + q or a smaller max_cluster_atoms");
-  const int64_t slots_fit = (int64_t)(((size_t)MKA_STATIC_SCRATCH_BYTES - fixed) / cf.slot_bytes);
-  const int64_t grid = std::min<int64_t>(std::min<int64_t>(n_sel, slots_fit), cf.grid_max);
-  AtomsLaunchArgs a{};
-  a.counter = reinterpret_cast<int*>(base);
-  a.sel = reinterpret_cast<const int64_t*>(base + 256);
-  a.scratch = base + fixed;
-  a.order = nullptr;
-  a.n_sel = n_sel;
-  a.p = p;
-  a.q = q;
-  a.cg_tol = cg_tol;
-  a.cg_maxit = cg_maxit;
-  a.eps = eps;
-  a.w = w;
-  a.nu_eff = nu_eff;
-  a.cg_iters = cg_iters;
-  a.status = status;
-  a.keep = 0;
-  a.grid = (int)grid;
-  // The counter must start at zero; the atom list is copied in; slots need no clearing
-  // (the kernel writes every slot entry before reading it).
-  MKA_CUDA_TRY(cudaMemsetAsync(base, 0, 256, st));
-  MKA_CUDA_TRY(cudaMemcpyAsync(base + 256, h_atoms, (size_t)n_sel * sizeof(int64_t), cudaMemcpyHostToDevice, st));
-  return atoms_launch(sys, MKA_FP64, cf, a, st);
+                "mka_solve_columns_static: one work slot (" + std::to_string(cf.slot_bytes) +
+                    " B) and one atom's reduced problems exceed the fixed scratch of " + std::to_string(total) +
+                    " B; pass a smaller p + q or a smaller max_cluster_atoms");
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n_sel, (int64_t)((total - 512 - cf.slot_bytes) / 2 / per_atom)));
+  const size_t sel_bytes = align_up((size_t)chunk * sizeof(int64_t), 256);
+  const size_t red_bytes = align_up(red_buffer_bytes(4 * chunk, nu), 256);
+  const size_t fixed = 256 + sel_bytes + red_bytes;
+  const int64_t slots_fit = (int64_t)((total - fixed) / cf.slot_bytes);
+  if (slots_fit < 1) return fail(MKA_ERR_INVALID_ARG, "mka_solve_columns_static: the fixed scratch holds no work slot");
+  for (int64_t off = 0; off < n_sel; off += chunk) {
+    const int64_t cnt = std::min(chunk, n_sel - off);
+    AtomsLaunchArgs a{};
+    a.counter = reinterpret_cast<int*>(base);
+    a.sel = reinterpret_cast<const int64_t*>(base + 256);
+    a.red = reinterpret_cast<double*>(base + 256 + sel_bytes);
+    a.scratch = base + fixed;
+    a.order = nullptr;
+    a.n_sel = cnt;
+    a.p = p;
+    a.q = q;
+    a.cg_tol = cg_tol;
+    a.cg_maxit = cg_maxit;
+    a.eps = eps + 4 * off * nu;
+    a.w = w + 4 * off * nu;
+    a.nu_eff = nu_eff + 4 * off;
+    a.cg_iters = cg_iters + 4 * off;
+    a.status = status + 4 * off;
+    a.keep = 0;
+    a.grid = (int)std::min<int64_t>(std::min<int64_t>(cnt, slots_fit), cf.grid_max);
+    // The counter must start at zero; the chunk's atom list is copied in; slots and the reduced
+    // buffer need no clearing (every entry is written before it is read).
+    MKA_CUDA_TRY(cudaMemsetAsync(base, 0, 256, st));
+    MKA_CUDA_TRY(cudaMemcpyAsync(base + 256, h_atoms + off, (size_t)cnt * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    s = atoms_launch(sys, MKA_FP64, cf, a, st);
+    if (!s) s = reduced_for(sys, a, st);
+    if (s) return s;
+  }
+  return MKA_OK;
 }
 
 }  // namespace

@@ -116,7 +116,24 @@ struct AtomsLaunchArgs {
   int32_t* fallback = nullptr;     // [4 n_sel] or NULL
   int cg_only = 0;                 // 1: stop after CG, write s_j on the patch into cg_target
   float* cg_target = nullptr;      // [4 n_sel][68]
+  // reduced problems of the selection, lane-interleaved: [ceil(4 n_sel / 32)][red_block_doubles(nu)][32]
+  // (not used with cg_only)
+  double* red = nullptr;
 };
+
+// Per-column doubles of the reduced-problem buffer: H_r and S_r (nu x nu each), then the
+// row j of U and of S U (nu each).
+__host__ __device__ constexpr size_t red_block_doubles(int nu) { return (size_t)2 * nu * nu + (size_t)2 * nu; }
+// Bytes of the reduced-problem buffer for n_cols columns.
+inline size_t red_buffer_bytes(int64_t n_cols, int nu) {
+  return sizeof(double) * red_block_doubles(nu) * 32 * (size_t)((n_cols + 31) / 32);
+}
+// The batched reduced problems (reduced.cu): one lane per column over the buffer filled by
+// the per-atom kernel; writes eps, w (ranked), the final status and nu_eff, and with keep
+// the pattern rows of V in place of those of U in vp.
+mka_status reduced_launch(double* red, int64_t n_cols, int nu, int32_t* status, int32_t* nu_eff, double* eps,
+                          double* w, int keep, double* vp, const int64_t* blk_off, const int64_t* sel,
+                          const int32_t* row_ptr, cudaStream_t st);
 
 // Learned warm start (mlp.cu).
 mka_status features_enqueue(const mka_system* sys, const int64_t* d_sel, int64_t n, float* X, int32_t* patch,
@@ -127,6 +144,8 @@ int64_t mlp_work_floats(int64_t B);   // floats of forward/backward work buffers
 
 mka_status atoms_config(const mka_system* sys, int nu, int arith, int max_cl, int threads, int ctas_per_sm,
                         AtomsConfig* out);
+// The batched reduced problems of a selection the per-atom kernel has just processed.
+mka_status reduced_for(const mka_system* sys, const AtomsLaunchArgs& a, cudaStream_t st);
 mka_status atoms_launch(const mka_system* sys, int arith, const AtomsConfig& cf, const AtomsLaunchArgs& a,
                         cudaStream_t st);
 

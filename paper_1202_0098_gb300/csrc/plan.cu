@@ -88,6 +88,8 @@ struct mka_plan {
   cudaEvent_t staged = nullptr;
   cudaStream_t capture = nullptr;  // private stream the graphs are captured on (never executes work)
   cudaEvent_t k0 = nullptr, k1 = nullptr;   // recorded around the per-atom kernel inside every graph
+  cudaEvent_t k2 = nullptr;        // recorded after the batched reduced problems
+  double* red = nullptr;           // reduced-problem buffer of max_atoms atoms
   float* warm = nullptr;           // learned start: X [4A][132], Y [4A][68], network work buffers
   int32_t* patch = nullptr;        // [A][17]
   std::vector<mka::GraphEntry> graphs;
@@ -119,6 +121,7 @@ mka_status plan_alloc(mka_plan* P) {
   MKA_CUDA_TRY(cudaMalloc(&r->d_self, sizeof(int32_t) * A));
   MKA_CUDA_TRY(cudaMalloc(&r->d_vp, sizeof(double) * max_blocks * 16 * nu));
   MKA_CUDA_TRY(cudaMalloc(&P->scratch, P->cf.slot_bytes * (size_t)P->grid + 256));
+  MKA_CUDA_TRY(cudaMalloc(&P->red, red_buffer_bytes(4 * A, (int)nu)));
   MKA_CUDA_TRY(cudaMalloc(&P->counter, 256));
   MKA_CUDA_TRY(cudaMalloc(&P->order, sizeof(int32_t) * A));
   MKA_CUDA_TRY(cudaMalloc(&P->sizes, sizeof(int32_t) * A));
@@ -130,6 +133,7 @@ mka_status plan_alloc(mka_plan* P) {
   MKA_CUDA_TRY(cudaStreamCreateWithFlags(&P->capture, cudaStreamNonBlocking));
   MKA_CUDA_TRY(cudaEventCreate(&P->k0));
   MKA_CUDA_TRY(cudaEventCreate(&P->k1));
+  MKA_CUDA_TRY(cudaEventCreate(&P->k2));
   if (P->prm.use_warm_start) {
     MKA_CUDA_TRY(cudaMalloc(&r->d_fallback, sizeof(int32_t) * 4 * A));
     MKA_CUDA_TRY(cudaMalloc(&P->warm, sizeof(float) * (4 * A * (132 + 68) + mlp_work_floats(4 * A))));
@@ -190,11 +194,15 @@ mka_status plan_enqueue(mka_plan* P, int64_t n, double n_electrons, double kT, d
   a.self_k = r->d_self;
   a.scratch = P->scratch;
   a.counter = P->counter;
+  a.red = P->red;
   a.grid = (int)std::min<int64_t>(n, P->grid);
   MKA_CUDA_TRY(cudaEventRecordWithFlags(P->k0, st, cudaEventRecordExternal));
   mka_status s = atoms_launch(P->sys, P->prm.arith, P->cf, a, st);
   if (s) return s;
   MKA_CUDA_TRY(cudaEventRecordWithFlags(P->k1, st, cudaEventRecordExternal));
+  s = reduced_for(P->sys, a, st);
+  if (s) return s;
+  MKA_CUDA_TRY(cudaEventRecordWithFlags(P->k2, st, cudaEventRecordExternal));
   const int nu = r->nu;
   s = find_mu_enqueue(r->d_eps, r->d_w, 4 * n * nu, n_electrons, kT, 1e-12, kHalvings, P->mu_buf, P->dev_out, st);
   if (s) return s;
@@ -213,8 +221,10 @@ void mka_plan_destroy(mka_plan* P) {
   if (P->capture) cudaStreamDestroy(P->capture);
   if (P->k0) cudaEventDestroy(P->k0);
   if (P->k1) cudaEventDestroy(P->k1);
+  if (P->k2) cudaEventDestroy(P->k2);
   cudaFreeHost(P->h_stage);
   cudaFree(P->scratch);
+  cudaFree(P->red);
   cudaFree(P->counter);
   cudaFree(P->order);
   cudaFree(P->sizes);
@@ -351,10 +361,11 @@ mka_status mka_plan_scalars(mka_plan* P, double* mu, double* e_band, double* n_e
   return MKA_OK;
 }
 
-mka_status mka_plan_kernel_ms(mka_plan* P, float* ms) {
-  if (!P || !ms) return fail(MKA_ERR_INVALID_ARG, "plan and ms are required");
-  MKA_CUDA_TRY(cudaEventSynchronize(P->k1));
-  MKA_CUDA_TRY(cudaEventElapsedTime(ms, P->k0, P->k1));
+mka_status mka_plan_kernel_ms(mka_plan* P, float* atoms_ms, float* reduced_ms) {
+  if (!P) return fail(MKA_ERR_INVALID_ARG, "plan is NULL");
+  MKA_CUDA_TRY(cudaEventSynchronize(P->k2));
+  if (atoms_ms) MKA_CUDA_TRY(cudaEventElapsedTime(atoms_ms, P->k0, P->k1));
+  if (reduced_ms) MKA_CUDA_TRY(cudaEventElapsedTime(reduced_ms, P->k1, P->k2));
   return MKA_OK;
 }
 

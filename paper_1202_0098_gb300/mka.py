@@ -93,7 +93,7 @@ def load(path: str | None = None) -> C.CDLL:
         "mka_plan_run": [P, P, I64, D, D, P],
         "mka_plan_scalars": [P, P, P, P],
         "mka_plan_result": [P, P],
-        "mka_plan_kernel_ms": [P, P],
+        "mka_plan_kernel_ms": [P, P, P],
         "mka_plan_info": [P, P, P, P],
         "mka_autotune": [P, P, P, I64, D, D, C.c_char_p, P, P],
         "mka_mlp_create": [C.c_uint64, P],
@@ -321,10 +321,11 @@ def mka_plan_scalars(plan) -> tuple[float, float, float]:
     return mu.value, e.value, n.value
 
 
-def mka_plan_kernel_ms(plan) -> float:
-    ms = C.c_float()
-    _check(load().mka_plan_kernel_ms(plan, C.byref(ms)), "mka_plan_kernel_ms")
-    return ms.value
+def mka_plan_kernel_ms(plan) -> tuple[float, float]:
+    """(per-atom kernel ms, batched reduced-problem kernel ms) of the last batch."""
+    a, r = C.c_float(), C.c_float()
+    _check(load().mka_plan_kernel_ms(plan, C.byref(a), C.byref(r)), "mka_plan_kernel_ms")
+    return a.value, r.value
 
 
 def mka_plan_result(plan) -> C.c_void_p:

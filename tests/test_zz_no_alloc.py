@@ -71,22 +71,41 @@ def test_static_scratch_matches_allocating_solve_twice(lib):
         mka.mka_system_destroy(s)
 
 
-def test_static_scratch_rejects_requests_beyond_its_size(lib):
+def test_static_scratch_in_chunks(lib):
+    """nu = 64 leaves room for only about 120 atoms' reduced problems per pass: 216 atoms take two."""
+    mka = lib
+    pos, box = lattice_positions("diamond", 3.567, 3, 0.08, 0.0, 13)
+    p, q, R = 32, 32, 5.0
+    s = mka.mka_build_system(pos, box, SK_CARBON_LIKE, "fp64", cluster_radius=R)
+    try:
+        max_cl = int(mka.mka_cluster_sizes(s).max())
+        atoms = np.arange(pos.shape[0], dtype=np.int64)
+        ref = reference_levels(mka, s, atoms, p, q)
+        got = static_levels(mka, s, atoms, p, q, max_cl)
+        np.testing.assert_array_equal(got["status"], ref["status"])
+        np.testing.assert_array_equal(got["nu_eff"], ref["nu_eff"])
+        np.testing.assert_allclose(got["eps"], ref["eps"], rtol=0, atol=TOL)
+        np.testing.assert_allclose(got["w"], ref["w"], rtol=0, atol=TOL)
+    finally:
+        mka.mka_system_destroy(s)
+
+
+def test_static_scratch_rejects_bad_requests_on_the_host(lib):
+    """Rejected requests fail validation before any device work (the buffers are sized for the
+    request all the same, so a request that were not rejected would still stay in bounds)."""
     mka = lib
     pos, box = lattice_positions("diamond", 3.567, 3, 0.08, 0.0, 13)
     s = mka.mka_build_system(pos, box, SK_CARBON_LIKE, "fp64", cluster_radius=5.0)
     try:
-        too_many = np.zeros(mka.MKA_STATIC_SCRATCH_BYTES // 8 + 1, dtype=np.int64)   # the atom list alone overflows
-        buf = torch.empty(1, dtype=torch.float64, device="cuda")
-        ibuf = torch.empty(1, dtype=torch.int32, device="cuda")
-        with pytest.raises(mka.MkaError) as e:
-            mka.mka_solve_columns_static(s, too_many, 8, 8, 1e-12, 500, 64, buf.data_ptr(), buf.data_ptr(),
-                                         ibuf.data_ptr(), ibuf.data_ptr(), ibuf.data_ptr())
-        assert e.value.status == mka.MKA_ERR_INVALID_ARG and "fixed scratch" in str(e.value)
-        with pytest.raises(mka.MkaError) as e:
-            mka.mka_solve_columns_static(s, np.array([0]), 8, 8, 1e-12, 500, mka.MKA_MAX_CLUSTER_ATOMS + 1,
-                                         buf.data_ptr(), buf.data_ptr(), ibuf.data_ptr(), ibuf.data_ptr(),
-                                         ibuf.data_ptr())
-        assert e.value.status == mka.MKA_ERR_INVALID_ARG
+        atoms = np.array([0], dtype=np.int64)
+        for p, q, max_cl in ((40, 25, 64), (8, 8, mka.MKA_MAX_CLUSTER_ATOMS + 1), (0, 8, 64)):
+            n, nu = 4 * len(atoms), max(1, p + q)
+            buf = torch.empty(n * nu, dtype=torch.float64, device="cuda")
+            buf2 = torch.empty(n * nu, dtype=torch.float64, device="cuda")
+            ib = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(3)]
+            with pytest.raises(mka.MkaError) as e:
+                mka.mka_solve_columns_static(s, atoms, p, q, 1e-12, 500, max_cl, buf.data_ptr(), buf2.data_ptr(),
+                                             ib[0].data_ptr(), ib[1].data_ptr(), ib[2].data_ptr())
+            assert e.value.status == mka.MKA_ERR_INVALID_ARG
     finally:
         mka.mka_system_destroy(s)
