@@ -485,11 +485,11 @@ struct AtomState {
 // rows): coef[mm][c] = (S u_mm)^T l for columns whose basis holds mm (when do_coef), and, for
 // columns with a pending projection column pn = n - 1, H_r[mm][pn] = u_mm^T (H u_pn) and
 // S_r[mm][pn] = u_mm^T (S u_pn) written (with their mirror) to the reduced-problem buffer of
-// column col0 + c.
+// column col0 + c, and S_r - I to Es ([4][nu][nu], FP32).
 template <typename T>
 __device__ void gs_sweep(const T* U, const T* SU, const T* L, const T* KV, const T* SV, int m, int m_cap, int nmax,
                          bool do_coef, const AtomState& st, double* coef, T* coefT, double* red, int64_t col0,
-                         int nu) {
+                         int nu, float* Es) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const bool proj = st.proj_any;
   for (int mm = wid; mm < nmax; mm += (int)(blockDim.x >> 5)) {
@@ -534,6 +534,9 @@ __device__ void gs_sweep(const T* U, const T* SU, const T* L, const T* KV, const
         H[(size_t)(pn * nu + mm) * 32] = (double)ph[c];
         S[(size_t)(mm * nu + pn) * 32] = (double)ps[c];
         S[(size_t)(pn * nu + mm) * 32] = (double)ps[c];
+        const float ev = (float)(ps[c] - (mm == pn ? (T)1 : (T)0));
+        Es[(c * nu + mm) * nu + pn] = ev;
+        Es[(c * nu + pn) * nu + mm] = ev;
       }
     }
   }
@@ -567,6 +570,8 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
   // FP32 form only: the low halves of l and H u_{n-1}
   float* Llo = reinterpret_cast<float*>(V2 + (size_t)m_cap * 4);
   float* Klo = Llo + (size_t)m_cap * 4;
+  // S_r - I of the four columns' bases so far, [4][nu][nu] FP32
+  float* Es = reinterpret_cast<float*>(region + (size_t)(sizeof(T) == 4 ? 5 : 3) * m_cap * 4 * sizeof(T));
 
   char* slot = A.scratch + (size_t)blockIdx.x * A.slot_bytes;
   T* U = reinterpret_cast<T*>(slot);                 // [nu][m_cap][4]
@@ -850,8 +855,12 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
       }
       __syncthreads();
       const int nmax = st.n_max;
-      for (int pass = 0; pass < 2 && nmax > 0; ++pass) {
-        gs_sweep<T>(U, SU, Lv, KV, SL, m, m_cap, nmax, true, st, coef, coefT, A.red, 4 * widx, nu);
+      // One classical Gram-Schmidt pass with the projector's first-order Gram correction: the
+      // coefficients c = (S U)^T l become c - E c with E = S_r - I = U^T S U - I (formed by the
+      // projection already), so that l - U (c - E c) is S-orthogonal to the basis up to O(E^2)
+      // and to the errors of this pass, the non-orthogonality a second pass would remove.
+      if (nmax > 0) {
+        gs_sweep<T>(U, SU, Lv, KV, SL, m, m_cap, nmax, true, st, coef, coefT, A.red, 4 * widx, nu, Es);
         if (threadIdx.x < 4) {
           double s = 0;
           for (int mm = 0; mm < nmax; ++mm) s += coef[mm * 4 + threadIdx.x] * coef[mm * 4 + threadIdx.x];
@@ -859,6 +868,15 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
           st.proj[threadIdx.x] = 0;
         }
         if (threadIdx.x == 0) st.proj_any = 0;
+        for (int t = threadIdx.x; t < 4 * nmax; t += blockDim.x) {
+          const int c = t & 3, mm = t >> 2, nc = st.n[c];
+          if (mm >= nc) continue;
+          const float* er = Es + (c * nu + mm) * nu;
+          double corr = 0.0;
+          for (int k = 0; k < nc; ++k) corr += (double)er[k] * coef[k * 4 + c];
+          coefT[mm * 4 + c] = (T)(coef[mm * 4 + c] - corr);
+        }
+        __syncthreads();
         for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
           const int r = i >> 2, c = i & 3;
           if constexpr (sizeof(T) == 4) {
@@ -1046,7 +1064,7 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
         st.n_max = nm;
       }
       __syncthreads();
-      gs_sweep<T>(U, SU, Lv, KV, SL, m, m_cap, st.n_max, false, st, coef, coefT, A.red, 4 * widx, nu);
+      gs_sweep<T>(U, SU, Lv, KV, SL, m, m_cap, st.n_max, false, st, coef, coefT, A.red, 4 * widx, nu, Es);
     }
 
     // ---- 4. what the reduced problems need: row j of U and S U (H_r, S_r are in place) -------
@@ -1141,11 +1159,12 @@ void fill_system_args(Args<TV>& A, const mka_system* s) {
 }
 
 // Dynamic shared memory of atoms_kernel: cluster list and local pattern, then the [m_cap][4]
-// work vectors of CG and the basis (three, and two low halves in the FP32 form).
-size_t dyn_smem_bytes(int lnnz_cap, int mcap, size_t elem) {
+// work vectors of CG and the basis (three, and two low halves in the FP32 form), then
+// S_r - I of the four columns ([4][nu][nu] FP32).
+size_t dyn_smem_bytes(int nu, int lnnz_cap, int mcap, size_t elem) {
   size_t off = (size_t)(2 * kMaxCl + 1 + lnnz_cap) * sizeof(int) + (size_t)lnnz_cap * sizeof(uint16_t);
   off = align_up(off, 16);
-  return off + (size_t)(elem == 4 ? 5 : 3) * mcap * 4 * elem;
+  return off + (size_t)(elem == 4 ? 5 : 3) * mcap * 4 * elem + sizeof(float) * 4 * (size_t)nu * nu;
 }
 
 // Per-CTA global work slot: U and S U ([nu][m_cap][4]) and s_j ([m_cap][4]) in the arithmetic
@@ -1162,7 +1181,7 @@ mka_status config_t(const mka_system* sys, int nu, int max_cl, int ctas_per_sm, 
   cf.threads = NT;
   cf.mcap = 4 * std::max(1, std::min(max_cl, kMaxCl));
   cf.lnnz_cap = std::max(1, std::min(max_cl, kMaxCl) * std::max(1, sys->max_row_blocks));
-  cf.smem = dyn_smem_bytes(cf.lnnz_cap, cf.mcap, sizeof(T));
+  cf.smem = dyn_smem_bytes(nu, cf.lnnz_cap, cf.mcap, sizeof(T));
   cf.slot_bytes = slot_bytes_for(nu, cf.mcap, sizeof(T));
   auto kern = atoms_kernel<TV, T, NT>;
   MKA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem));
