@@ -77,6 +77,9 @@ WORKLOADS = {
     "diamond1m": Workload("diamond1m", "diamond", 3.567, 50, 0.15, 0.0, 3, SK_CARBON_LIKE, 7.0, 20, 20, 0.1),
     # 10,077,696-atom diamond (108^3 cells), the one-GPU full-scale system.
     "diamond10m": Workload("diamond10m", "diamond", 3.567, 108, 0.1, 0.0, 5, SK_CARBON_LIKE, 6.0, 15, 15, 0.1),
+    # 262,144-atom cut of the same material (32^3 cells): the per-atom work of diamond10m on a
+    # system small enough for full profiler captures.
+    "diamond262k": Workload("diamond262k", "diamond", 3.567, 32, 0.1, 0.0, 6, SK_CARBON_LIKE, 6.0, 15, 15, 0.1),
 }
 
 _BASIS = {
