@@ -60,6 +60,40 @@ def dist_env():
     return rank, world, local
 
 
+# ---- multi-rank host logic (weak scaling: each rank its own atoms, no collective on the data path) ----
+
+def shard_atoms(rank, i, n_steps, B, N):
+    """Atoms of step i on `rank`: consecutive blocks of B atoms, rank-major, wrapping around the system."""
+    start = ((rank * n_steps + i) * B) % N
+    return np.arange(start, start + B, dtype=np.int64) % N
+
+
+def max_over_ranks(x, device="cpu"):
+    """The largest of the ranks' values of x (x itself on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def job_throughput(columns_per_rank_step, steps, world, max_ms):
+    """Whole-job columns/s: the columns all ranks processed over the slowest rank's time."""
+    return columns_per_rank_step * steps * world / (max_ms / 1e3)
+
+
+def workload_desc(name, w, N):
+    return f"{name}: {N} atoms, {4 * N} columns, R={w.R} A, p=q={w.p}, kT={w.kT} eV"
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
 
@@ -156,7 +190,9 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: FP64 CPU oracle, {per_step} random atoms per step"},
+            "config": {"workload": workload_desc(args.workload, w, pos.shape[0]),
+                       "form": "FP64 oracle on FP64 values, host cores", "atoms_per_step": per_step,
+                       "sample": f"{per_step} random atoms per step"},
             "cpu_baseline": {"value": val, "unit": "columns/s", "cores": cores, "kind": "oracle",
                              "sample": f"{per_step} random atoms ({cols} columns) of {args.workload} per step"},
             "e2e": {"value": val, "unit": "columns/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -274,6 +310,7 @@ def run_form(mka, torch, sysh, w, form, B, batch_atoms, steps, warmup, stream, t
     for i in range(warmup):
         mka.mka_plan_run(plan, batch_atoms(i), n_e, w.kT, rho.data_ptr())
     torch.cuda.synchronize()
+    rank_barrier()
     out = {"tuning": mka.mka_plan_info(plan)}
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kms, mus, ebs = [], [], []
@@ -286,6 +323,7 @@ def run_form(mka, torch, sysh, w, form, B, batch_atoms, steps, warmup, stream, t
         kms.append(mka.mka_plan_kernel_ms(plan))      # waits for this batch's column kernels only
     t1.record(stream)
     torch.cuda.synchronize()
+    rank_barrier()
     torch.cuda.nvtx.range_pop()
     out["launches"] = mka.mka_kernel_launches() - launches0
     out["ms"] = t0.elapsed_time(t1)
@@ -332,8 +370,7 @@ def main():
     n_steps = args.warmup + args.steps
 
     def batch_atoms(i):
-        start = ((rank * n_steps + i) * B) % N
-        return np.arange(start, start + B, dtype=np.int64) % N
+        return shard_atoms(rank, i, n_steps, B, N)
 
     compare = list(range(args.warmup, args.warmup + max(1, min(args.steps, 3))))
     learned = form == "mixed" and not args.no_learned
@@ -343,12 +380,8 @@ def main():
         mka.mka_system_set_warm_start(sysh, net)
     main_run = run_form(mka, torch, sysh, w, form, B, batch_atoms, args.steps, args.warmup, stream, tune_cache, rank,
                         not args.no_autotune, compare, learned)
-    ms = main_run["ms"]
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = 4 * B * args.steps * world / (ms / 1e3)
+    ms = max_over_ranks(main_run["ms"], "cuda")
+    value = job_throughput(4 * B, args.steps, world, ms)
 
     # clocks during a second pass of the same timed batches
     clocks = ClockSampler(local)
@@ -365,6 +398,7 @@ def main():
     if not args.no_e2e:
         rho_h = torch.empty(main_run["rho"].numel(), dtype=torch.float64, pin_memory=True)
         torch.cuda.synchronize()
+        rank_barrier()
         te = time.perf_counter()
         d2h = 0
         for i in range(args.warmup, n_steps):
@@ -375,8 +409,10 @@ def main():
             rho_h[:nb * 16].copy_(main_run["rho"][:nb * 16])
             d2h += nb * 16 * 8 + sum(v.nbytes for k, v in lv.items() if hasattr(v, "nbytes")) + 24
         torch.cuda.synchronize()
-        te = time.perf_counter() - te
-        e2e = {"value": 4 * B * args.steps * world / te, "unit": "columns/s", "h2d_bytes_per_step": 16 * B + 8,
+        rank_barrier()
+        te = max_over_ranks(time.perf_counter() - te, "cuda")
+        e2e = {"value": job_throughput(4 * B, args.steps, world, 1e3 * te), "unit": "columns/s",
+               "h2d_bytes_per_step": 16 * B + 8,
                "d2h_bytes_per_step": d2h // args.steps}
 
     # the mixed form without the learned start on the same batches: what the network gains
@@ -384,14 +420,14 @@ def main():
         fsteps = max(1, min(args.steps, 3))
         prun = run_form(mka, torch, sysh, w, "mixed", B, batch_atoms, fsteps, 1, stream, tune_cache, rank,
                         not args.no_autotune, compare, False)
-        pval = 4 * B * fsteps / (prun["ms"] / 1e3)
+        pval = job_throughput(4 * B, fsteps, world, max_over_ranks(prun["ms"], "cuda"))
         # both plans' rho buffers on the same (last compared) batch
         last = batch_atoms(compare[-1])
         mka.mka_plan_run(main_run["plan"], last, w.electrons_per_atom * B, w.kT, main_run["rho"].data_ptr())
         torch.cuda.synchronize()
         nb = mka.mka_result_info(mka.mka_plan_result(prun["plan"]))["n_blocks"]
         learn_info.update({
-            "plain_mixed_value": pval, "speedup_over_plain_mixed": value / world / pval,
+            "plain_mixed_value": pval, "speedup_over_plain_mixed": value / pval,
             "cg_iters_plain": prun["cg_iters"], "cg_iters_learned": main_run["cg_iters"],
             "fallback_rate": main_run["fallback_rate"],
             "max_abs_drho_vs_plain": float((main_run["rho"][:nb * 16] - prun["rho"][:nb * 16]).abs().max().item()),
@@ -405,11 +441,11 @@ def main():
         fsteps = max(1, min(args.steps, 3))
         frun = run_form(mka, torch, sysh, w, "fp64", B, batch_atoms, fsteps, 1, stream, tune_cache, rank,
                         not args.no_autotune, compare)
-        fval = 4 * B * fsteps / (frun["ms"] / 1e3)
+        fval = job_throughput(4 * B, fsteps, world, max_over_ranks(frun["ms"], "cuda"))
         de = max(abs(a - b) for a, b in zip(main_run["e_band"], frun["e_band"])) / B
         dmu = max(abs(a - b) for a, b in zip(main_run["mu"], frun["mu"]))
         other = {"form": "fp64", "value": fval, "unit": "columns/s", "steps": fsteps,
-                 "speedup_of_headline": value / world / fval, "compared_batches": len(compare),
+                 "speedup_of_headline": value / fval, "compared_batches": len(compare),
                  "max_abs_dE_eV_per_atom": de, "max_abs_dmu_eV": dmu,
                  "tuning": frun["tuning"], "kernel_ms_mean": statistics.mean(frun["kernel_ms"])}
         mka.mka_plan_destroy(frun["plan"])
@@ -444,8 +480,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if form == "fp64" else "f32",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {N} atoms, {4 * N} columns, R={w.R} A, p=q={w.p}, "
-                                   f"kT={w.kT} eV, {form}{'+learned' if learned else ''} form, {storage}-stored H and S",
+            "config": {"workload": workload_desc(args.workload, w, N),
+                       "form": f"{form}{'+learned' if learned else ''}, {storage}-stored H and S",
                        "atoms_per_step": B, "columns_per_step": 4 * B,
                        "step": "one graph-replayed batch: per-atom kernel, mu bisection over the batch, rho, E",
                        "l2": "inputs larger than L2 (H,S of the whole system in HBM; each step a new batch of atoms)",
