@@ -460,6 +460,100 @@ __device__ void spmm4_pair(const TV* __restrict__ val, const int* lrow, const ui
   __syncthreads();
 }
 
+// yH = H x and yS = S x in one pass over the shared block pattern (x read once), for the
+// columns in `mask`; FP64 form.
+template <typename TV, typename T>
+__device__ void spmm4_hs(const TV* __restrict__ valH, const TV* __restrict__ valS, const int* lrow,
+                         const uint16_t* lcol, const int* lblk, int ncl, const T* __restrict__ x, T* __restrict__ yH,
+                         T* __restrict__ yS, int mask) {
+  for (int r = threadIdx.x; r < 4 * ncl; r += blockDim.x) {
+    const int t = r >> 2, i = r & 3;
+    T h[4] = {0, 0, 0, 0}, s[4] = {0, 0, 0, 0};
+    const int e1 = lrow[t + 1];
+#pragma unroll 2
+    for (int e = lrow[t]; e < e1; ++e) {
+      T vh[4], vs[4];
+      RowLoad<TV, T>::load(valH, lblk[e], i, vh);
+      RowLoad<TV, T>::load(valS, lblk[e], i, vs);
+      const T* xb = x + (size_t)lcol[e] * 16;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        T xk[4];
+        ld4(xb + 4 * k, xk);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          h[q] += vh[k] * xk[q];
+          s[q] += vs[k] * xk[q];
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (mask >> q & 1) {
+        yH[4 * r + q] = h[q];
+        yS[4 * r + q] = s[q];
+      }
+  }
+  __syncthreads();
+}
+
+// The FP32-pair form of spmm4_hs: x = xh + xl; H x as a pair (yHh + yHl), S x rounded once to
+// yS, both with error-free products and compensated sums on the hi part (as spmm4_pair).
+template <typename TV>
+__device__ void spmm4_pair_hs(const TV* __restrict__ valH, const TV* __restrict__ valS, const int* lrow,
+                              const uint16_t* lcol, const int* lblk, int ncl, const float* __restrict__ xh,
+                              const float* __restrict__ xl, float* __restrict__ yHh, float* __restrict__ yHl,
+                              float* __restrict__ yS, int mask) {
+  for (int row = threadIdx.x; row < 4 * ncl; row += blockDim.x) {
+    const int t = row >> 2, i = row & 3;
+    float hh[4] = {0, 0, 0, 0}, hl[4] = {0, 0, 0, 0}, sh[4] = {0, 0, 0, 0}, sl[4] = {0, 0, 0, 0};
+    const int e1 = lrow[t + 1];
+    for (int e = lrow[t]; e < e1; ++e) {
+      float vh[4], vs[4];
+      RowLoad<TV, float>::load(valH, lblk[e], i, vh);
+      RowLoad<TV, float>::load(valS, lblk[e], i, vs);
+      const float* xb = xh + (size_t)lcol[e] * 16;
+      const float* xc = xl + (size_t)lcol[e] * 16;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        float xk[4], xs[4];
+        ld4(xb + 4 * k, xk);
+        ld4(xc + 4 * k, xs);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          {
+            const float p = __fmul_rn(vh[k], xk[q]);
+            const float pe = fmaf(vh[k], xk[q], -p);
+            const float s = __fadd_rn(hh[q], p);
+            const float bb = __fsub_rn(s, hh[q]);
+            const float err = __fadd_rn(__fsub_rn(hh[q], __fsub_rn(s, bb)), __fsub_rn(p, bb));
+            hh[q] = s;
+            hl[q] = __fadd_rn(hl[q], __fadd_rn(err, fmaf(vh[k], xs[q], pe)));
+          }
+          {
+            const float p = __fmul_rn(vs[k], xk[q]);
+            const float pe = fmaf(vs[k], xk[q], -p);
+            const float s = __fadd_rn(sh[q], p);
+            const float bb = __fsub_rn(s, sh[q]);
+            const float err = __fadd_rn(__fsub_rn(sh[q], __fsub_rn(s, bb)), __fsub_rn(p, bb));
+            sh[q] = s;
+            sl[q] = __fadd_rn(sl[q], __fadd_rn(err, fmaf(vs[k], xs[q], pe)));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (!(mask >> q & 1)) continue;
+      const float s = __fadd_rn(hh[q], hl[q]);
+      yHh[4 * row + q] = s;
+      yHl[4 * row + q] = __fsub_rn(hl[q], __fsub_rn(s, hh[q]));
+      yS[4 * row + q] = __fadd_rn(sh[q], sl[q]);
+    }
+  }
+  __syncthreads();
+}
+
 // Per-column dot products over the cluster rows: per-thread partial sums in T
 // (a few terms each), combined across threads in FP64.
 template <typename T>
@@ -544,7 +638,7 @@ __device__ void gs_sweep(const T* U, const T* SU, const T* L, const T* KV, const
 }
 
 template <typename TV, typename T, int NT>
-__global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
+__global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ AtomState st;
   __shared__ double red[2 * kMaxWarps * 4];
@@ -959,11 +1053,13 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
         }
       }
       const int amask = st.active[0] | (st.active[1] << 1) | (st.active[2] << 2) | (st.active[3] << 3);
-      // S l; in the FP32 form from the pair, rounded once, so that S_r is the Gram matrix of the basis kept
+      // S l and H l in one pass (H u_n = H l / beta for an accepted l); in the FP32 form from the
+      // pair, S l rounded once so that S_r is the Gram matrix of the basis kept, H l as a pair.
+      // KV held H u of the last accepted vector, whose projection the sweep above has taken.
       if constexpr (sizeof(T) == 4)
-        spmm4_pair<TV>(A.valS, lrow, lcol, lblk, ncl, Lv, Llo, SL, nullptr, amask);
+        spmm4_pair_hs<TV>(A.valH, A.valS, lrow, lcol, lblk, ncl, Lv, Llo, KV, Klo, SL, amask);
       else
-        spmm4<TV, T>(A.valS, lrow, lcol, lblk, ncl, Lv, SL, amask);
+        spmm4_hs<TV, T>(A.valH, A.valS, lrow, lcol, lblk, ncl, Lv, KV, SL, amask);
       dot4<T>(Lv, SL, m, red, sums);
       if (threadIdx.x < 4) {
         const int c = threadIdx.x;
@@ -997,28 +1093,29 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
           if (st.accept[c]) {
             const T bi = scal[8 + c];
             T u = Lv[i] * bi;
+            T k = KV[i] * bi;
             const T su = SL[i] * bi;
             const size_t o = (size_t)st.n[c] * m_cap * 4 + 4 * r + c;
-            if constexpr (sizeof(T) == 4) {   // u_n as an FP32 pair
+            if constexpr (sizeof(T) == 4) {   // u_n and H u_n as FP32 pairs
               const float ul = __fadd_rn(fmaf(Lv[i], bi, -u), __fmul_rn(Llo[i], bi));
               const float s = __fadd_rn(u, ul);
               const float lo = __fsub_rn(ul, __fsub_rn(s, u));
               u = s;
               Ulo[o] = lo;
               Llo[i] = lo;
+              const float kl = __fadd_rn(fmaf(KV[i], bi, -k), __fmul_rn(Klo[i], bi));
+              const float ks = __fadd_rn(k, kl);
+              Klo[i] = __fsub_rn(kl, __fsub_rn(ks, k));
+              k = ks;
             }
             U[o] = u;
             SU[o] = su;
             Lv[i] = u;
+            KV[i] = k;                // H u_n
             SL[i] = su;               // S u_n, kept for the projection column
           }
         }
         __syncthreads();
-        // H u_n, accepted columns only (as an FP32 pair in the FP32 form)
-        if constexpr (sizeof(T) == 4)
-          spmm4_pair<TV>(A.valH, lrow, lcol, lblk, ncl, Lv, Llo, KV, Klo, acc_mask);
-        else
-          spmm4<TV, T>(A.valH, lrow, lcol, lblk, ncl, Lv, KV, acc_mask);
       }
       if (threadIdx.x < 4) {
         const int c = threadIdx.x;
@@ -1039,6 +1136,24 @@ __global__ void __launch_bounds__(NT) atoms_kernel(const Args<TV> A) {
       }
       if (threadIdx.x == 0) st.proj_any = acc_mask != 0;
       __syncthreads();
+      // s_j dropped as already in the span: the next vector is H u_n of the last accepted u_n,
+      // recomputed here from the stored basis (KV now holds H applied to the dropped s_j)
+      const int kmask = (st.act[0] == ACT_LOAD_K) | ((st.act[1] == ACT_LOAD_K) << 1) |
+                        ((st.act[2] == ACT_LOAD_K) << 2) | ((st.act[3] == ACT_LOAD_K) << 3);
+      if (kmask) {
+        for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
+          const int r = i >> 2, c = i & 3;
+          if (!(kmask >> c & 1)) continue;
+          const size_t o = (size_t)(st.n[c] - 1) * m_cap * 4 + 4 * r + c;
+          Lv[i] = U[o];
+          if constexpr (sizeof(T) == 4) Llo[i] = Ulo[o];
+        }
+        __syncthreads();
+        if constexpr (sizeof(T) == 4)
+          spmm4_pair<TV>(A.valH, lrow, lcol, lblk, ncl, Lv, Llo, KV, Klo, kmask);
+        else
+          spmm4<TV, T>(A.valH, lrow, lcol, lblk, ncl, Lv, KV, kmask);
+      }
       for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
         const int c = i & 3;
         if (!st.active[c]) continue;
