@@ -590,6 +590,7 @@ __device__ void gs_sweep(const T* U, const T* SU, const T* L, const T* KV, const
     const T* su = SU + (size_t)mm * m_cap * 4;
     const T* u = U + (size_t)mm * m_cap * 4;
     T pc[4] = {0, 0, 0, 0}, ph[4] = {0, 0, 0, 0}, ps[4] = {0, 0, 0, 0};
+#pragma unroll 2
     for (int r = lane; r < m; r += 32) {
       if (do_coef) {
 #pragma unroll
