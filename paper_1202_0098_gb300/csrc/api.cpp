@@ -60,7 +60,7 @@ void mka_result_destroy(mka_result* r) {
   cudaFree(r->d_cg_iters);
   cudaFree(r->d_status);
   cudaFree(r->d_vp);
-  cudaFree(r->d_self);
+  cudaFree(r->d_cv);
   cudaFree(r->d_mu_state);
   cudaFree(r->d_fallback);
   delete r;
@@ -112,9 +112,9 @@ mka_status mka_solve_columns(mka_system* sys, const int64_t* atoms, int64_t n_se
   ALLOC(r->d_nu_eff, sizeof(int32_t) * nc);
   ALLOC(r->d_cg_iters, sizeof(int32_t) * nc);
   ALLOC(r->d_status, sizeof(int32_t) * nc);
-  ALLOC(r->d_self, sizeof(int32_t) * r->n_sel);
   if (prm->use_warm_start) ALLOC(r->d_fallback, sizeof(int32_t) * nc);
   if (r->keep) ALLOC(r->d_vp, sizeof(double) * r->n_blocks * 16 * nu);
+  if (r->keep) ALLOC(r->d_cv, kept_buffer_bytes(nc, (int)nu));
 #undef ALLOC
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(r->d_sel, r->h_sel.data(), sizeof(int64_t) * r->n_sel, cudaMemcpyHostToDevice, st);

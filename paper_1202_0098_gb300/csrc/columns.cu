@@ -137,7 +137,6 @@ struct Args {
   int keep;
   double* vp;
   const int64_t* blk_off;
-  int32_t* self_k;
   // learned warm start: predicted s_j on the 17-atom patch, or NULL for x0 = 0
   const float* x0;          // [4 n_sel][68]
   const int32_t* patch;     // [n_sel][17] atom ids (-1: none)
@@ -699,6 +698,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
         A.nu_eff[col] = 0;
         A.cg_iters[col] = 0;
       }
+      if (A.keep) {
+        const int nrow = A.row_ptr[atom + 1] - A.row_ptr[atom];
+        double* vpa = A.vp + A.blk_off[widx] * 16 * (int64_t)nu;
+        for (int i = threadIdx.x; i < nrow * 16 * nu; i += blockDim.x) vpa[i] = 0.0;
+      }
       __syncthreads();
       continue;
     }
@@ -724,6 +728,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
         A.status[4 * widx + c] = ST_TOOLARGE;
         A.nu_eff[4 * widx + c] = 0;
         A.cg_iters[4 * widx + c] = 0;
+      }
+      if (A.keep) {
+        const int nrow = A.row_ptr[atom + 1] - A.row_ptr[atom];
+        double* vpa = A.vp + A.blk_off[widx] * 16 * (int64_t)nu;
+        for (int i = threadIdx.x; i < nrow * 16 * nu; i += blockDim.x) vpa[i] = 0.0;
       }
       __syncthreads();
       continue;
@@ -1214,12 +1223,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
         const int k = (int)(lblk[e] - rbase);
         vpa[((int64_t)k * 16 + c * 4 + r) * nu + n] = (double)U[(size_t)n * m_cap * 4 + 4 * (4 * (int)lcol[e] + r) + c];
       }
-      if (threadIdx.x == 0) {
-        int sk = -1;
-        for (int e = e0; e < e0 + ne; ++e)
-          if (lcol[e] == t0) sk = (int)(lblk[e] - rbase);
-        A.self_k[widx] = sk;
-      }
     }
     __syncthreads();
   }
@@ -1339,7 +1342,6 @@ mka_status launch_t(const mka_system* sys, const AtomsConfig& cf, const AtomsLau
   A.keep = a.keep;
   A.vp = a.vp;
   A.blk_off = a.blk_off;
-  A.self_k = a.self_k;
   A.x0 = a.x0;
   A.patch = a.patch;
   A.fallback = a.fallback;
@@ -1389,8 +1391,8 @@ mka_status atoms_config(const mka_system* sys, int nu, int arith, int max_cl, in
 }
 
 mka_status reduced_for(const mka_system* sys, const AtomsLaunchArgs& a, cudaStream_t st) {
-  return reduced_launch(a.red, 4 * a.n_sel, a.p + a.q, a.status, a.nu_eff, a.eps, a.w, a.keep, a.vp, a.blk_off, a.sel,
-                        sys->d_row_ptr, st);
+  return reduced_launch(a.red, 4 * a.n_sel, a.p + a.q, a.status, a.nu_eff, a.eps, a.w, a.keep ? a.cv : nullptr,
+                        a.col0, st);
 }
 
 mka_status atoms_launch(const mka_system* sys, int arith, const AtomsConfig& cf, const AtomsLaunchArgs& a,
@@ -1456,7 +1458,8 @@ mka_status launch_columns(mka_system* sys, mka_result* res, const mka_solve_para
     a.keep = res->keep;
     a.vp = res->d_vp;
     a.blk_off = res->keep ? res->d_blk_off + off : nullptr;
-    a.self_k = res->keep ? res->d_self + off : nullptr;
+    a.cv = res->d_cv;
+    a.col0 = 4 * off;
     a.scratch = scratch;
     a.counter = counter;
     a.red = red;

@@ -144,31 +144,46 @@ __global__ void mu_init_kernel(MuState* S, unsigned* ticket, double target, doub
 
 __global__ void mu_finish_kernel(const MuState* S, double* mu_out) { *mu_out = 0.5 * (S->lo + S->hi); }
 
-// rho / E: one CTA per selected atom, thread per (block k, c, r) of its row.
-__global__ void density_kernel(const double* vp, const double* eps, const int64_t* blk_off, const int32_t* self_k,
+// Column c of atom t: g = C diag(x) V_j for per-level weights x (ascending order of eps), from the
+// kept C and V_j (lane-interleaved by column); thread per (c, n), g into shared memory [4][nu].
+__device__ void column_weights(const double* cv, int64_t t, int nu, const double* x, double* g) {
+  for (int i = threadIdx.x; i < 4 * nu; i += blockDim.x) {
+    const int c = i / nu, n = i % nu;
+    const int64_t col = 4 * t + c;
+    const double* b = cv + (size_t)(col >> 5) * kept_block_doubles(nu) * 32 + (col & 31);
+    double s = 0.0;
+    for (int a = 0; a < nu; ++a) s += b[(size_t)(n * nu + a) * 32] * x[c * nu + a] * b[(size_t)(nu * nu + a) * 32];
+    g[i] = s;
+  }
+  __syncthreads();
+}
+
+// rho / E: one CTA per selected atom, thread per (block k, c, r) of its row:
+// rho_ij = sum_alpha f_alpha V_i alpha V_j alpha = U_i . g_j with g_j = C diag(f) V_j.
+__global__ void density_kernel(const double* vp, const double* cv, const double* eps, const int64_t* blk_off,
                                const int64_t* sel, const int32_t* row_ptr, const void* valH, int storage,
                                int nu, double mu_host, const double* mu_dev, double kT, double* rho,
                                double* e_partial) {
   __shared__ double red[kRedThreads / 32];
   __shared__ double f[4 * MKA_MAX_NU];
+  __shared__ double g[4 * MKA_MAX_NU];
   const double mu = mu_dev ? *mu_dev : mu_host;
   const int64_t t = blockIdx.x;
   const int64_t atom = sel[t];
   const int nrow = row_ptr[atom + 1] - row_ptr[atom];
   const int64_t b0 = blk_off[t];
-  const int sk = self_k[t];
   for (int i = threadIdx.x; i < 4 * nu; i += blockDim.x) {
     const int c = i / nu;
     f[i] = fermi(eps[(4 * t + c) * nu + i % nu], mu, kT);
   }
   __syncthreads();
+  column_weights(cv, t, nu, f, g);
   double e = 0.0;
   for (int i = threadIdx.x; i < nrow * 16; i += blockDim.x) {
     const int k = i >> 4, c = (i >> 2) & 3, r = i & 3;
-    const double* v = vp + ((b0 + k) * 16 + c * 4 + r) * (int64_t)nu;
-    const double* vj = vp + ((b0 + sk) * 16 + c * 4 + c) * (int64_t)nu;
+    const double* u = vp + ((b0 + k) * 16 + c * 4 + r) * (int64_t)nu;
     double s = 0.0;
-    for (int a = 0; a < nu; ++a) s += f[c * nu + a] * v[a] * vj[a];
+    for (int n = 0; n < nu; ++n) s += u[n] * g[c * nu + n];
     if (rho) rho[(b0 + k) * 16 + c * 4 + r] = s;
     const int64_t gk = (int64_t)row_ptr[atom] + k;
     double h;
@@ -181,31 +196,31 @@ __global__ void density_kernel(const double* vp, const double* eps, const int64_
   if (threadIdx.x == 0) e_partial[t] = 2.0 * s;
 }
 
-__global__ void greens_kernel(const double* vp, const double* eps, const int64_t* blk_off, const int32_t* self_k,
+// G_ij(z) = sum_alpha V_i alpha V_j alpha / (z - eps_alpha) = U_i . (C diag(1 / (z - eps)) V_j).
+__global__ void greens_kernel(const double* vp, const double* cv, const double* eps, const int64_t* blk_off,
                               const int64_t* sel, const int32_t* row_ptr, int nu, double zr, double zi, double* g) {
-  __shared__ double gr[4 * MKA_MAX_NU], gi[4 * MKA_MAX_NU];
+  __shared__ double xr[4 * MKA_MAX_NU], xi[4 * MKA_MAX_NU], gr[4 * MKA_MAX_NU], gi[4 * MKA_MAX_NU];
   const int64_t t = blockIdx.x;
   const int64_t atom = sel[t];
   const int nrow = row_ptr[atom + 1] - row_ptr[atom];
   const int64_t b0 = blk_off[t];
-  const int sk = self_k[t];
   for (int i = threadIdx.x; i < 4 * nu; i += blockDim.x) {
     const int c = i / nu;
     const double dr = zr - eps[(4 * t + c) * nu + i % nu];
     const double den = dr * dr + zi * zi;   // 1 / (z - e) = (dr - i zi) / den
-    gr[i] = dr / den;
-    gi[i] = -zi / den;
+    xr[i] = dr / den;
+    xi[i] = -zi / den;
   }
   __syncthreads();
+  column_weights(cv, t, nu, xr, gr);
+  column_weights(cv, t, nu, xi, gi);
   for (int i = threadIdx.x; i < nrow * 16; i += blockDim.x) {
     const int k = i >> 4, c = (i >> 2) & 3, r = i & 3;
-    const double* v = vp + ((b0 + k) * 16 + c * 4 + r) * (int64_t)nu;
-    const double* vj = vp + ((b0 + sk) * 16 + c * 4 + c) * (int64_t)nu;
+    const double* u = vp + ((b0 + k) * 16 + c * 4 + r) * (int64_t)nu;
     double sr = 0.0, si = 0.0;
-    for (int a = 0; a < nu; ++a) {
-      const double pv = v[a] * vj[a];
-      sr += pv * gr[c * nu + a];
-      si += pv * gi[c * nu + a];
+    for (int n = 0; n < nu; ++n) {
+      sr += u[n] * gr[c * nu + n];
+      si += u[n] * gi[c * nu + n];
     }
     g[2 * ((b0 + k) * 16 + c * 4 + r)] = sr;
     g[2 * ((b0 + k) * 16 + c * 4 + r) + 1] = si;
@@ -366,10 +381,10 @@ mka_status find_mu_enqueue(const double* eps, const double* w, int64_t n, double
   return MKA_OK;
 }
 
-mka_status density_enqueue(const mka_system* sys, const int64_t* sel, const int64_t* blk_off, const int32_t* self_k,
-                           const double* vp, const double* eps, const double* w, int64_t n_sel, int nu,
+mka_status density_enqueue(const mka_system* sys, const int64_t* sel, const int64_t* blk_off, const double* vp,
+                           const double* cv, const double* eps, const double* w, int64_t n_sel, int nu,
                            const double* mu_dev, double kT, double* rho_out, double* tmp, cudaStream_t st) {
-  density_kernel<<<(unsigned)n_sel, 128, 0, st>>>(vp, eps, blk_off, self_k, sel, sys->d_row_ptr, sys->d_valH,
+  density_kernel<<<(unsigned)n_sel, 128, 0, st>>>(vp, cv, eps, blk_off, sel, sys->d_row_ptr, sys->d_valH,
                                                   sys->storage, nu, 0.0, mu_dev, kT, rho_out, tmp);
   sum_kernel<<<1, kRedThreads, 0, st>>>(tmp, n_sel, tmp + n_sel);
   count_partial_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(eps, w, 4 * n_sel * nu, 0.0, mu_dev, kT, tmp + n_sel + 2);
@@ -419,7 +434,7 @@ mka_status launch_density(mka_system* sys, mka_result* res, double mu, double kT
   cudaStream_t st = res->stream;
   double* tmp = nullptr;
   MKA_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(double) * (res->n_sel + 2 + kRedBlocks), st));
-  density_kernel<<<(unsigned)res->n_sel, 128, 0, st>>>(res->d_vp, res->d_eps, res->d_blk_off, res->d_self,
+  density_kernel<<<(unsigned)res->n_sel, 128, 0, st>>>(res->d_vp, res->d_cv, res->d_eps, res->d_blk_off,
                                                        res->d_sel, sys->d_row_ptr, sys->d_valH, sys->storage,
                                                        res->nu, mu, nullptr, kT, rho_out, tmp);
   sum_kernel<<<1, kRedThreads, 0, st>>>(tmp, res->n_sel, tmp + res->n_sel);
@@ -443,7 +458,7 @@ mka_status launch_density(mka_system* sys, mka_result* res, double mu, double kT
 }
 
 mka_status launch_greens(mka_system* sys, mka_result* res, double z_re, double z_im, double* g_out) {
-  greens_kernel<<<(unsigned)res->n_sel, 128, 0, res->stream>>>(res->d_vp, res->d_eps, res->d_blk_off, res->d_self,
+  greens_kernel<<<(unsigned)res->n_sel, 128, 0, res->stream>>>(res->d_vp, res->d_cv, res->d_eps, res->d_blk_off,
                                                                res->d_sel, sys->d_row_ptr, res->nu, z_re, z_im, g_out);
   count_launches();
   MKA_CUDA_TRY(cudaGetLastError());

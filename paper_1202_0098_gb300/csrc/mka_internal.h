@@ -70,8 +70,8 @@ struct mka_result {
   int32_t* d_nu_eff = nullptr;
   int32_t* d_cg_iters = nullptr;
   int32_t* d_status = nullptr;
-  double* d_vp = nullptr;         // kept pattern rows [n_blocks][4 c][4 r][nu]
-  int32_t* d_self = nullptr;      // [n_sel] index (within the atom's row) of its diagonal block
+  double* d_vp = nullptr;         // kept pattern rows of U [n_blocks][4 c][4 r][nu]
+  double* d_cv = nullptr;         // kept C and V_j, lane-interleaved [n_cols / 32][kept_block_doubles][32]
   double* d_mu_state = nullptr;   // bisection bracket and partial sums
   int32_t* d_fallback = nullptr;  // [n_cols] warm-start fallback flags (learned start only)
   std::vector<int64_t> h_sel;
@@ -107,7 +107,6 @@ struct AtomsLaunchArgs {
   int keep = 0;
   double* vp = nullptr;
   const int64_t* blk_off = nullptr;
-  int32_t* self_k = nullptr;
   char* scratch = nullptr;         // grid x slot_bytes
   int* counter = nullptr;          // zero in stream order before the launch
   int grid = 0;
@@ -119,21 +118,29 @@ struct AtomsLaunchArgs {
   // reduced problems of the selection, lane-interleaved: [ceil(4 n_sel / 32)][red_block_doubles(nu)][32]
   // (not used with cg_only)
   double* red = nullptr;
+  // kept C and V_j (NULL: not kept), lane-interleaved by absolute column index col0 + local column
+  double* cv = nullptr;
+  int64_t col0 = 0;
 };
 
 // Per-column doubles of the reduced-problem buffer: H_r and S_r (nu x nu each), then the
 // row j of U and of S U (nu each).
 __host__ __device__ constexpr size_t red_block_doubles(int nu) { return (size_t)2 * nu * nu + (size_t)2 * nu; }
+// Per-column doubles of the kept reduced solution: C (nu x nu, columns in ascending order of
+// eps) and the row V_j = (row j of U) C; rho_ij = U_i . (C diag(f) V_j).
+__host__ __device__ constexpr size_t kept_block_doubles(int nu) { return (size_t)nu * nu + (size_t)nu; }
+inline size_t kept_buffer_bytes(int64_t n_cols, int nu) {
+  return sizeof(double) * kept_block_doubles(nu) * 32 * (size_t)((n_cols + 31) / 32);
+}
 // Bytes of the reduced-problem buffer for n_cols columns.
 inline size_t red_buffer_bytes(int64_t n_cols, int nu) {
   return sizeof(double) * red_block_doubles(nu) * 32 * (size_t)((n_cols + 31) / 32);
 }
 // The batched reduced problems (reduced.cu): one lane per column over the buffer filled by
-// the per-atom kernel; writes eps, w (ranked), the final status and nu_eff, and with keep
-// the pattern rows of V in place of those of U in vp.
+// the per-atom kernel; writes eps, w (ranked), the final status and nu_eff, and (cv != NULL)
+// the kept C and V_j of column col0 + c.
 mka_status reduced_launch(double* red, int64_t n_cols, int nu, int32_t* status, int32_t* nu_eff, double* eps,
-                          double* w, int keep, double* vp, const int64_t* blk_off, const int64_t* sel,
-                          const int32_t* row_ptr, cudaStream_t st);
+                          double* w, double* cv, int64_t col0, cudaStream_t st);
 
 // Learned warm start (mlp.cu).
 mka_status features_enqueue(const mka_system* sys, const int64_t* d_sel, int64_t n, float* X, int32_t* patch,
@@ -165,8 +172,8 @@ mka_status launch_spmv(const mka_system* sys, int which, int x_dtype, const void
 size_t mu_buffer_bytes();
 mka_status find_mu_enqueue(const double* eps, const double* w, int64_t n, double n_electrons, double kT, double tol,
                            int halvings, void* buf, double* mu_dev_out, cudaStream_t st);
-mka_status density_enqueue(const mka_system* sys, const int64_t* sel, const int64_t* blk_off, const int32_t* self_k,
-                           const double* vp, const double* eps, const double* w, int64_t n_sel, int nu,
+mka_status density_enqueue(const mka_system* sys, const int64_t* sel, const int64_t* blk_off, const double* vp,
+                           const double* cv, const double* eps, const double* w, int64_t n_sel, int nu,
                            const double* mu_dev, double kT, double* rho_out, double* tmp, cudaStream_t st);
 // tmp of density_enqueue holds n_sel + 2 + kDensityTmpExtra doubles.
 constexpr int kDensityTmpExtra = 608;

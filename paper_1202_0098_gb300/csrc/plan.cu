@@ -118,8 +118,8 @@ mka_status plan_alloc(mka_plan* P) {
   MKA_CUDA_TRY(cudaMalloc(&r->d_nu_eff, sizeof(int32_t) * 4 * A));
   MKA_CUDA_TRY(cudaMalloc(&r->d_cg_iters, sizeof(int32_t) * 4 * A));
   MKA_CUDA_TRY(cudaMalloc(&r->d_status, sizeof(int32_t) * 4 * A));
-  MKA_CUDA_TRY(cudaMalloc(&r->d_self, sizeof(int32_t) * A));
   MKA_CUDA_TRY(cudaMalloc(&r->d_vp, sizeof(double) * max_blocks * 16 * nu));
+  MKA_CUDA_TRY(cudaMalloc(&r->d_cv, kept_buffer_bytes(4 * A, (int)nu)));
   MKA_CUDA_TRY(cudaMalloc(&P->scratch, P->cf.slot_bytes * (size_t)P->grid + 256));
   MKA_CUDA_TRY(cudaMalloc(&P->red, red_buffer_bytes(4 * A, (int)nu)));
   MKA_CUDA_TRY(cudaMalloc(&P->counter, 256));
@@ -191,10 +191,11 @@ mka_status plan_enqueue(mka_plan* P, int64_t n, double n_electrons, double kT, d
   a.keep = 1;
   a.vp = r->d_vp;
   a.blk_off = r->d_blk_off;
-  a.self_k = r->d_self;
   a.scratch = P->scratch;
   a.counter = P->counter;
   a.red = P->red;
+  a.cv = r->d_cv;
+  a.col0 = 0;
   a.grid = (int)std::min<int64_t>(n, P->grid);
   MKA_CUDA_TRY(cudaEventRecordWithFlags(P->k0, st, cudaEventRecordExternal));
   mka_status s = atoms_launch(P->sys, P->prm.arith, P->cf, a, st);
@@ -206,7 +207,7 @@ mka_status plan_enqueue(mka_plan* P, int64_t n, double n_electrons, double kT, d
   const int nu = r->nu;
   s = find_mu_enqueue(r->d_eps, r->d_w, 4 * n * nu, n_electrons, kT, 1e-12, kHalvings, P->mu_buf, P->dev_out, st);
   if (s) return s;
-  return density_enqueue(P->sys, r->d_sel, r->d_blk_off, r->d_self, r->d_vp, r->d_eps, r->d_w, n, nu, P->dev_out, kT,
+  return density_enqueue(P->sys, r->d_sel, r->d_blk_off, r->d_vp, r->d_cv, r->d_eps, r->d_w, n, nu, P->dev_out, kT,
                          rho_out, P->dev_out + 1, st);
 }
 

@@ -7,7 +7,9 @@
 // Householder tridiagonalisation A = Q T Q^T, implicit-shift QL on T with the rotations
 // accumulated into Z = Q, C = L^{-T} Z. The outputs of a column are its levels eps_alpha
 // in ascending order, w_alpha = V_{j alpha} (S V)_{j alpha} with V = U C (Eq. EQ-DM's
-// weights), and, when vectors are kept, the pattern rows of V.
+// weights), and, when vectors are kept, C and the row V_j = (row j of U) C in the same order:
+// rho_ij = sum_alpha f_alpha V_i alpha V_j alpha = U_i . (C diag(f) V_j) and G_ij(z) likewise,
+// so the kept pattern rows of U never need turning into rows of V.
 //
 // These solves are short chains of dependent FP64 operations (square roots, divisions,
 // the QL recurrence), and the FP64 pipe of an SM issues one warp instruction every 16
@@ -34,11 +36,8 @@ struct RedArgs {
   int32_t* nu_eff;           // in: basis size; out: subspace dimension used (0 on failure)
   double* eps;               // [n_cols][nu]
   double* w;                 // [n_cols][nu]
-  int keep;
-  double* vp;                // pattern rows of U on entry, of V = U C on return
-  const int64_t* blk_off;    // [n_cols / 4] first pattern block of each atom
-  const int64_t* sel;        // [n_cols / 4] atoms
-  const int32_t* row_ptr;    // BSR row pointers of the system
+  double* cv;                // kept C and V_j (NULL: not kept), lane-interleaved by column col0 + col
+  int64_t col0;
 };
 
 // Element (i, j) of the lane's matrices: H_r / Z / C at (i nu + j), S_r / L at nu^2 + (i nu + j).
@@ -270,35 +269,29 @@ __global__ void __launch_bounds__(128) reduced_kernel(const RedArgs A) {
       epsc[rank[a]] = d[a];
       wc[rank[a]] = vj * svj;
     }
-  if (A.keep) {                        // pattern rows of V = U C, in place, ranked
-    const int64_t t = col >> 2;
-    const int c = (int)(col & 3);
-    const int64_t atom = A.sel[t];
-    const int nrow = A.row_ptr[atom + 1] - A.row_ptr[atom];
-    for (int k = 0; k < nrow; ++k)
-      for (int r = 0; r < 4; ++r) {
-        double* row = A.vp + ((A.blk_off[t] + k) * 16 + c * 4 + r) * (int64_t)nu;
-        if (ok) {
-          for (int i = 0; i < n; ++i) e[i] = row[i];
-          for (int a = 0; a < n; ++a) {
-            double v = 0.0;
-            for (int i = 0; i < n; ++i) v += e[i] * M.H(i, a);
-            p[rank[a]] = v;
-          }
-          for (int a = 0; a < n; ++a) row[a] = p[a];
-          for (int a = n; a < nu; ++a) row[a] = 0.0;
-        } else {
-          for (int a = 0; a < nu; ++a) row[a] = 0.0;
-        }
+  if (A.cv) {                           // C and V_j, columns ranked, zero beyond nu_eff
+    const int64_t ca = A.col0 + col;
+    double* out = A.cv + (size_t)(ca >> 5) * kept_block_doubles(nu) * 32 + (ca & 31);
+    const int ne = ok ? n : 0;
+    int* inv = reinterpret_cast<int*>(tau);   // tau is free after the solve: rank -> eigenvector
+    for (int a = 0; a < ne; ++a) inv[rank[a]] = a;
+    if (ok)
+      for (int a = 0; a < ne; ++a) {      // V_j alpha = (row j of U) . c_alpha
+        double v = 0.0;
+        for (int k = 0; k < ne; ++k) v += M.UJ(k) * M.H(k, a);
+        e[a] = v;
       }
+    for (int r = 0; r < nu; ++r)
+      for (int a = 0; a < nu; ++a)
+        out[(size_t)(r * nu + a) * 32] = (r < ne && a < ne) ? M.H(r, inv[a]) : 0.0;
+    for (int a = 0; a < nu; ++a) out[(size_t)(nu * nu + a) * 32] = a < ne ? e[inv[a]] : 0.0;
   }
 }
 
 }  // namespace
 
 mka_status reduced_launch(double* blk, int64_t n_cols, int nu, int32_t* status, int32_t* nu_eff, double* eps,
-                          double* w, int keep, double* vp, const int64_t* blk_off, const int64_t* sel,
-                          const int32_t* row_ptr, cudaStream_t st) {
+                          double* w, double* cv, int64_t col0, cudaStream_t st) {
   if (n_cols <= 0) return MKA_OK;
   RedArgs A{};
   A.blk = blk;
@@ -308,11 +301,8 @@ mka_status reduced_launch(double* blk, int64_t n_cols, int nu, int32_t* status, 
   A.nu_eff = nu_eff;
   A.eps = eps;
   A.w = w;
-  A.keep = keep;
-  A.vp = vp;
-  A.blk_off = blk_off;
-  A.sel = sel;
-  A.row_ptr = row_ptr;
+  A.cv = cv;
+  A.col0 = col0;
   const int threads = 128;
   reduced_kernel<<<(unsigned)((n_cols + threads - 1) / threads), threads, 0, st>>>(A);
   count_launches();
