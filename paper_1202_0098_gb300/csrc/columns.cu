@@ -815,13 +815,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
       st.cg_active[threadIdx.x] = sqrt(st.rr[threadIdx.x]) > A.cg_tol;
     }
     __syncthreads();
-    // Phase 0: CG to the tolerance. Phases 1 and 2 (FP32 arithmetic only): x is carried in FP64,
-    // its true residual, recomputed with error-free products and compensated sums (x as an FP32
-    // pair), replaces the recursive one and CG on the correction continues until the residual has
-    // dropped 1000-fold; two such rounds leave s_j accurate far below FP32 rounding. The seam
-    // vector is s_j minus its projection on K_p(H; e_j), of which s_j is mostly made, so its
-    // relative accuracy is that of s_j divided by the small remainder.
-    constexpr int kPhases = sizeof(T) == 4 ? 3 : 1;
+    // Phase 0: CG to the tolerance. Phase 1 (FP32 arithmetic only): x is carried in FP64, its true
+    // residual, recomputed with error-free products and compensated sums (x as an FP32 pair),
+    // replaces the recursive one and CG on the correction continues until that residual has
+    // dropped 10^6-fold (at most 20 iterations), which leaves s_j accurate far below FP32
+    // rounding. The seam vector is s_j minus its projection on K_p(H; e_j), of which s_j is mostly
+    // made, so its relative accuracy is that of s_j divided by the small remainder.
+    constexpr int kPhases = sizeof(T) == 4 ? 2 : 1;
     for (int phase = 0; phase < kPhases; ++phase) {
       int maxit = A.cg_maxit;
       if (phase >= 1) {
@@ -843,7 +843,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
         if (threadIdx.x < 4) {
           const int c = threadIdx.x;
           st.rr[c] = sums[c];
-          st.cg_stop[c] = 1e-3 * sqrt(sums[c]);
+          st.cg_stop[c] = 1e-6 * sqrt(sums[c]);
           st.cg_active[c] = (st.status[c] == ST_OK) && sums[c] > 0.0;
         }
         __syncthreads();
@@ -1015,7 +1015,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
       }
       if constexpr (sizeof(T) == 4) {
         // the seam vector in FP64: two classical Gram-Schmidt passes on s_j (FP64) for the columns
-        // whose l is s_j, replacing what the FP32 passes above made of them
+        // whose l is s_j, replacing what the FP32 pass above made of them
         const int smask = (st.active[0] && st.src[0] == SRC_S) | ((st.active[1] && st.src[1] == SRC_S) << 1) |
                           ((st.active[2] && st.src[2] == SRC_S) << 2) | ((st.active[3] && st.src[3] == SRC_S) << 3);
         if (smask && nmax > 0) {
