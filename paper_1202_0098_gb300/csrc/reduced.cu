@@ -68,19 +68,24 @@ __device__ bool lane_cholesky(const Lane& M, int n, double* rdiag) {
   return true;
 }
 
-// H <- L^{-1} H L^{-T} (full storage), symmetrised.
-__device__ void lane_congruence(const Lane& M, int n, const double* rdiag) {
-  for (int i = 0; i < n; ++i)          // X = L^{-1} H, row i from rows 0..i-1
+// H <- L^{-1} H L^{-T} (full storage), symmetrised. `row` (n doubles, lane-local) holds the
+// row of L, then of A, that an inner loop reuses.
+__device__ void lane_congruence(const Lane& M, int n, const double* rdiag, double* row) {
+  for (int i = 0; i < n; ++i) {        // X = L^{-1} H, row i from rows 0..i-1
+    for (int k = 0; k < i; ++k) row[k] = M.S(i, k);
     for (int j = 0; j < n; ++j) {
       double v = M.H(i, j);
-      for (int k = 0; k < i; ++k) v -= M.S(i, k) * M.H(k, j);
+      for (int k = 0; k < i; ++k) v -= row[k] * M.H(k, j);
       M.H(i, j) = v * rdiag[i];
     }
+  }
   for (int i = 0; i < n; ++i)          // A = X L^{-T}, column j from columns 0..j-1
     for (int j = 0; j < n; ++j) {
       double v = M.H(i, j);
-      for (int k = 0; k < j; ++k) v -= M.H(i, k) * M.S(j, k);
-      M.H(i, j) = v * rdiag[j];
+      for (int k = 0; k < j; ++k) v -= row[k] * M.S(j, k);
+      v *= rdiag[j];
+      row[j] = v;
+      M.H(i, j) = v;
     }
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < i; ++j) {
@@ -91,17 +96,22 @@ __device__ void lane_congruence(const Lane& M, int n, const double* rdiag) {
 }
 
 // Householder reduction T = Q^T A Q: diagonal d, off-diagonal e (e[k] couples k, k+1;
-// e[n-1] = 0); Q accumulated in place of A.
-__device__ void lane_tridiag(const Lane& M, int n, double* d, double* e, double* p, double* tau) {
+// e[n-1] = 0); Q accumulated in place of A. v (n doubles, lane-local) holds the current
+// Householder vector.
+__device__ void lane_tridiag(const Lane& M, int n, double* d, double* e, double* p, double* tau, double* v) {
   for (int k = 0; k + 2 < n; ++k) {
     double s2 = 0.0;
-    for (int i = k + 1; i < n; ++i) s2 += M.H(i, k) * M.H(i, k);
-    const double x0 = M.H(k + 1, k);
+    for (int i = k + 1; i < n; ++i) {
+      v[i] = M.H(i, k);
+      s2 += v[i] * v[i];
+    }
+    const double x0 = v[k + 1];
     const double nrm = sqrt(s2);
     const double alpha = x0 >= 0.0 ? -nrm : nrm;
     const double v0 = x0 - alpha;
     const double vtv = s2 - x0 * x0 + v0 * v0;
     const double tk = vtv > 0.0 ? 2.0 / vtv : 0.0;          // H_k = I - tk v v^T
+    v[k + 1] = v0;
     M.H(k + 1, k) = v0;                                       // v = A[k+1.., k]
     d[k] = M.H(k, k);
     e[k] = alpha;
@@ -109,15 +119,15 @@ __device__ void lane_tridiag(const Lane& M, int n, double* d, double* e, double*
     double pv = 0.0;
     for (int i = k + 1; i < n; ++i) {                         // p = tk B v
       double acc = 0.0;
-      for (int j = k + 1; j < n; ++j) acc += M.H(i, j) * M.H(j, k);
+      for (int j = k + 1; j < n; ++j) acc += M.H(i, j) * v[j];
       p[i] = tk * acc;
-      pv += p[i] * M.H(i, k);
+      pv += p[i] * v[i];
     }
     const double kc = 0.5 * tk * pv;
-    for (int i = k + 1; i < n; ++i) p[i] -= kc * M.H(i, k);   // w = p - kc v
+    for (int i = k + 1; i < n; ++i) p[i] -= kc * v[i];        // w = p - kc v
     for (int i = k + 1; i < n; ++i) {                         // B -= v w^T + w v^T
-      const double vi = M.H(i, k), wi = p[i];
-      for (int j = k + 1; j < n; ++j) M.H(i, j) -= vi * p[j] + wi * M.H(j, k);
+      const double vi = v[i], wi = p[i];
+      for (int j = k + 1; j < n; ++j) M.H(i, j) -= vi * p[j] + wi * v[j];
     }
   }
   if (n >= 2) {
@@ -139,13 +149,14 @@ __device__ void lane_tridiag(const Lane& M, int n, double* d, double* e, double*
     }
     const double tk = tau[k];
     if (tk != 0.0) {
-      for (int j = b; j < n; ++j) {    // p_j = tk sum_i v_i Q_ij
-        double y = 0.0;
-        for (int i = b; i < n; ++i) y += M.H(i, k) * M.H(i, j);
-        p[j] = tk * y;
+      for (int i = b; i < n; ++i) v[i] = M.H(i, k);
+      for (int j = b; j < n; ++j) p[j] = 0.0;
+      for (int i = b; i < n; ++i) {    // p_j = tk sum_i v_i Q_ij, row by row
+        const double vi = v[i];
+        for (int j = b; j < n; ++j) p[j] += vi * M.H(i, j);
       }
       for (int i = b; i < n; ++i) {
-        const double vi = M.H(i, k);
+        const double vi = tk * v[i];
         for (int j = b; j < n; ++j) M.H(i, j) -= vi * p[j];
       }
     }
@@ -223,24 +234,26 @@ __global__ void __launch_bounds__(128) reduced_kernel(const RedArgs A) {
   if (col >= A.n_cols) return;
   const int nu = A.nu;
   const Lane M{A.blk + (size_t)(col >> 5) * red_block_doubles(nu) * 32 + (col & 31), nu};
-  double d[MKA_MAX_NU], e[MKA_MAX_NU], rdiag[MKA_MAX_NU], p[MKA_MAX_NU], tau[MKA_MAX_NU];
+  double d[MKA_MAX_NU], e[MKA_MAX_NU], rdiag[MKA_MAX_NU], p[MKA_MAX_NU], tau[MKA_MAX_NU], v[MKA_MAX_NU];
   int rank[MKA_MAX_NU];
   const int n = A.nu_eff[col];
   const int st_in = A.status[col];
   bool ok = st_in == RS_OK && n > 0 && n <= nu;
   if (ok) ok = lane_cholesky(M, n, rdiag);
   if (ok) {
-    lane_congruence(M, n, rdiag);
-    lane_tridiag(M, n, d, e, p, tau);
+    lane_congruence(M, n, rdiag, v);
+    lane_tridiag(M, n, d, e, p, tau, v);
     ok = lane_tql(M, n, d, e, p, tau);   // p, tau reused as the rotation record
   }
   if (ok) {
-    for (int a = 0; a < n; ++a)        // C = L^{-T} Z, column a by back substitution
+    for (int a = 0; a < n; ++a) {      // C = L^{-T} Z, column a by back substitution (kept in v)
       for (int i = n - 1; i >= 0; --i) {
-        double v = M.H(i, a);
-        for (int k = i + 1; k < n; ++k) v -= M.S(k, i) * M.H(k, a);
-        M.H(i, a) = v * rdiag[i];
+        double s = M.H(i, a);
+        for (int k = i + 1; k < n; ++k) s -= M.S(k, i) * v[k];
+        v[i] = s * rdiag[i];
       }
+      for (int i = 0; i < n; ++i) M.H(i, a) = v[i];
+    }
     for (int a = 0; a < n; ++a) {
       int r = 0;
       for (int k = 0; k < n; ++k) r += (d[k] < d[a]) || (d[k] == d[a] && k < a);
