@@ -34,14 +34,13 @@
 // of its S-norm, so any perturbation of the first chain at FP32 rounding level
 // turns the direction the second chain starts from by about 100 times as much.
 // The basis is therefore carried as FP32 pairs (hi + lo, about 48 significant
-// bits): H u and S u take error-free FP32 products and compensated sums on the
-// hi part, the Gram-Schmidt update likewise, and only products with the lo
-// parts are rounded. s_j is refined to FP64 accuracy by CG on the true residual
-// (computed the same way) and orthogonalised in FP64 at the seam. The
-// Gram-Schmidt coefficients and the projected matrices are taken from the hi
-// parts (their errors stay inside the span or enter the reduced problem
-// unmagnified); the reduced solve, the mu bisection and all cross-thread sums
-// are FP64.
+// bits): H u takes error-free FP32 products and compensated sums on the hi part,
+// the Gram-Schmidt update likewise, and only products with the lo parts are
+// rounded. s_j is refined to FP64 accuracy by CG on the true residual (computed
+// the same way) and orthogonalised in FP64 at the seam. S u, the Gram-Schmidt
+// coefficients and the projected matrices are plain FP32 from the hi parts
+// (their errors stay inside the span or enter the reduced problem unmagnified);
+// the reduced solve, the mu bisection and all cross-thread sums are FP64.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -496,8 +495,9 @@ __device__ void spmm4_hs(const TV* __restrict__ valH, const TV* __restrict__ val
   __syncthreads();
 }
 
-// The FP32-pair form of spmm4_hs: x = xh + xl; H x as a pair (yHh + yHl), S x rounded once to
-// yS, both with error-free products and compensated sums on the hi part (as spmm4_pair).
+// The FP32-pair form of spmm4_hs: x = xh + xl; H x as a pair (yHh + yHl) with error-free
+// products and compensated sums on the hi part (as spmm4_pair); S x in plain FP32 from the hi
+// part (S u enters the coefficients, whose errors stay in the span, and S_r, unmagnified).
 template <typename TV>
 __device__ void spmm4_pair_hs(const TV* __restrict__ valH, const TV* __restrict__ valS, const int* lrow,
                               const uint16_t* lcol, const int* lblk, int ncl, const float* __restrict__ xh,
@@ -505,7 +505,7 @@ __device__ void spmm4_pair_hs(const TV* __restrict__ valH, const TV* __restrict_
                               float* __restrict__ yS, int mask) {
   for (int row = threadIdx.x; row < 4 * ncl; row += blockDim.x) {
     const int t = row >> 2, i = row & 3;
-    float hh[4] = {0, 0, 0, 0}, hl[4] = {0, 0, 0, 0}, sh[4] = {0, 0, 0, 0}, sl[4] = {0, 0, 0, 0};
+    float hh[4] = {0, 0, 0, 0}, hl[4] = {0, 0, 0, 0}, sh[4] = {0, 0, 0, 0};
     const int e1 = lrow[t + 1];
     for (int e = lrow[t]; e < e1; ++e) {
       float vh[4], vs[4];
@@ -529,15 +529,7 @@ __device__ void spmm4_pair_hs(const TV* __restrict__ valH, const TV* __restrict_
             hh[q] = s;
             hl[q] = __fadd_rn(hl[q], __fadd_rn(err, fmaf(vh[k], xs[q], pe)));
           }
-          {
-            const float p = __fmul_rn(vs[k], xk[q]);
-            const float pe = fmaf(vs[k], xk[q], -p);
-            const float s = __fadd_rn(sh[q], p);
-            const float bb = __fsub_rn(s, sh[q]);
-            const float err = __fadd_rn(__fsub_rn(sh[q], __fsub_rn(s, bb)), __fsub_rn(p, bb));
-            sh[q] = s;
-            sl[q] = __fadd_rn(sl[q], __fadd_rn(err, fmaf(vs[k], xs[q], pe)));
-          }
+          sh[q] = fmaf(vs[k], xk[q], sh[q]);
         }
       }
     }
@@ -547,7 +539,7 @@ __device__ void spmm4_pair_hs(const TV* __restrict__ valH, const TV* __restrict_
       const float s = __fadd_rn(hh[q], hl[q]);
       yHh[4 * row + q] = s;
       yHl[4 * row + q] = __fsub_rn(hl[q], __fsub_rn(s, hh[q]));
-      yS[4 * row + q] = __fadd_rn(sh[q], sl[q]);
+      yS[4 * row + q] = sh[q];
     }
   }
   __syncthreads();
@@ -1063,8 +1055,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
         }
       }
       const int amask = st.active[0] | (st.active[1] << 1) | (st.active[2] << 2) | (st.active[3] << 3);
-      // S l and H l in one pass (H u_n = H l / beta for an accepted l); in the FP32 form from the
-      // pair, S l rounded once so that S_r is the Gram matrix of the basis kept, H l as a pair.
+      // S l and H l in one pass (H u_n = H l / beta for an accepted l); in the FP32 form H l as a
+      // pair from the pair, S l in FP32.
       // KV held H u of the last accepted vector, whose projection the sweep above has taken.
       if constexpr (sizeof(T) == 4)
         spmm4_pair_hs<TV>(A.valH, A.valS, lrow, lcol, lblk, ncl, Lv, Llo, KV, Klo, SL, amask);
