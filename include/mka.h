@@ -94,9 +94,12 @@ typedef struct {
   int use_warm_start; /* 1: CG starts from the learned guess (see mka_mlp_*), 0: from zero */
   double cg_tol;      /* inner CG stops at ||r||_2 <= cg_tol ||e_j||_2 */
   int cg_maxit;       /* inner CG iteration cap (MKA_ERR_NO_CONVERGENCE beyond it) */
-  int keep_vectors;   /* 1: keep the pattern rows of v_alpha so that rho and G can be
-                         evaluated later for any mu / z (needs 16 nu doubles per block
-                         of the selected rows); 0: keep only (eps, w) */
+  int keep_vectors;   /* 1: keep what rho and G need to be evaluated later for any mu / z:
+                         the basis U on the pattern rows (16 nu doubles per block of the
+                         selected rows) and per column the reduced eigenvectors C and
+                         the row V_j = (row j of U) C (nu^2 + nu doubles), since
+                         sum_alpha x_alpha v_alpha,i v_alpha,j = U_i . (C diag(x) V_j);
+                         0: keep only (eps, w) */
 } mka_solve_params;
 
 /* ---- system ------------------------------------------------------------ */
@@ -308,7 +311,7 @@ typedef struct mka_plan mka_plan; /* every buffer of one batch of the work flow,
 
 /* A plan for batches of up to `max_atoms` atoms of `sys` (4 columns each): the
  * whole work flow of Eq. EQ-WORK-FLOW for one batch (the per-column brace with
- * kept pattern rows, mu by bisection over the batch's columns, rho and the band
+ * kept data as for keep_vectors, mu by bisection over the batch's columns, rho and the band
  * energy) with every buffer allocated here, once. `tune` may be NULL (defaults,
  * or pass the result of mka_autotune). The plan computes the largest cluster of
  * the whole system once, to size its work slots. Work runs on `stream`. */
