@@ -12,13 +12,14 @@
 //   3. the S-orthonormal basis of K_p(H; e_j) (+) K_q(H; s_j): S-orthogonalise,
 //      normalise, k_n = H u_n, next vector k_n or s_j after u_p (Eqs.
 //      EQ-REC-UN, EQ-KN-HUN, EQ-MGram-Schmidt, EQ-CALC-S-INV); Gram-Schmidt is
-//      the classical form run twice, coefficients (S u_m)^T l with S u_m kept;
+//      one classical pass, coefficients (S u_m)^T l with S u_m kept, corrected to
+//      first order by S_r - I (the seam vector gets two full FP64 passes);
 //   4. the projection H_r = U^T K, S_r = U^T (S U), accumulated while the basis
-//      grows, and the reduced generalized problem (Eq. EQ-SUB-EIG-VEC), one
-//      warp per column in FP64: Cholesky of S_r, L^{-1} H_r L^{-T}, Householder
-//      tridiagonalisation, implicit QL, C = L^{-T} Y;
-//   5. per column: ascending eps_alpha, w_alpha = V_{j alpha} (S V)_{j alpha},
-//      and (optionally) the pattern rows of V for rho and G.
+//      grows, written with row j of U and S U to the reduced-problem buffer;
+//      the reduced generalized problem (Eq. EQ-SUB-EIG-VEC) and the per-column
+//      outputs are the batched kernel of reduced.cu;
+//   5. with kept vectors, the pattern rows of U (rho and G are
+//      U_i . (C diag(x) V_j) from them and the reduced kernel's C and V_j).
 // Breakdown rule: a new vector that keeps no more than 1e-10 of its S-norm
 // (S-norm before projection taken from the Pythagorean sum of the removed
 // coefficients) is dropped; a dropped s_j is replaced by H u_n, a first chain
@@ -1202,7 +1203,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
       A.cg_iters[col] = st.it[c];
     }
     if (A.keep) {
-      // pattern rows of U (zero outside the cluster); the reduced pass turns them into rows of V = U C
+      // pattern rows of U (zero outside the cluster): rho_ij = U_i . (C diag(f) V_j)
       const int64_t rbase = A.row_ptr[atom];
       const int nrow = A.row_ptr[atom + 1] - A.row_ptr[atom];
       double* vpa = A.vp + A.blk_off[widx] * 16 * (int64_t)nu;
