@@ -650,15 +650,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
   uint16_t* lcol = reinterpret_cast<uint16_t*>(lblk + A.lnnz_cap);        // lnnz_cap
   size_t off = (size_t)(2 * kMaxCl + 1 + A.lnnz_cap) * sizeof(int) + (size_t)A.lnnz_cap * sizeof(uint16_t);
   off = (off + 15) & ~(size_t)15;
-  unsigned char* region = smem_raw + off;   // work vectors of CG and the basis
+  // Shared memory holds the vector the SpMV gathers through the cluster pattern; the vectors
+  // that are only streamed row by row live in the CTA's global slot.
+  unsigned char* region = smem_raw + off;
   T* V0 = reinterpret_cast<T*>(region);     // CG: p     basis: l
-  T* V1 = V0 + (size_t)m_cap * 4;           // CG: S p   basis: S l, then S u_{n-1}
-  T* V2 = V1 + (size_t)m_cap * 4;           // CG: r     basis: H u_{n-1}
-  // FP32 form only: the low halves of l and H u_{n-1}
-  float* Llo = reinterpret_cast<float*>(V2 + (size_t)m_cap * 4);
-  float* Klo = Llo + (size_t)m_cap * 4;
-  // S_r - I of the four columns' bases so far, [4][nu][nu] FP32
-  float* Es = reinterpret_cast<float*>(region + (size_t)(sizeof(T) == 4 ? 5 : 3) * m_cap * 4 * sizeof(T));
+  // FP32 form only: the low half of l
+  float* Llo = reinterpret_cast<float*>(V0 + (size_t)m_cap * 4);
 
   char* slot = A.scratch + (size_t)blockIdx.x * A.slot_bytes;
   T* U = reinterpret_cast<T*>(slot);                 // [nu][m_cap][4]
@@ -666,8 +663,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
   T* SJ = SU + (size_t)nu * m_cap * 4;               // s_j, [m_cap][4]
   double* SJd = reinterpret_cast<double*>(slot + align_up(sizeof(T) * ((size_t)2 * nu + 1) * m_cap * 4, 256));
   (void)SJd;   // FP32 arithmetic only: s_j in FP64 for the seam [m_cap][4]
-  // FP32 arithmetic only: low halves of the basis vectors [nu][m_cap][4]
-  float* Ulo = reinterpret_cast<float*>(reinterpret_cast<char*>(SJd) + align_up(sizeof(double) * 4 * (size_t)m_cap, 256));
+  // S_r - I of the four columns' bases so far, [4][nu][nu] FP32
+  float* Es = reinterpret_cast<float*>(reinterpret_cast<char*>(SJd) + align_up(sizeof(double) * 4 * (size_t)m_cap, 256));
+  T* V1 = reinterpret_cast<T*>(reinterpret_cast<char*>(Es) + align_up(sizeof(float) * 4 * (size_t)nu * nu, 256));
+  T* V2 = V1 + (size_t)m_cap * 4;   // V1: CG S p, basis S l then S u_{n-1}; V2: CG r, basis H u_{n-1}
+  // FP32 arithmetic only: the low half of H u_{n-1} [m_cap][4], low halves of the basis [nu][m_cap][4]
+  float* Klo = reinterpret_cast<float*>(V2 + (size_t)m_cap * 4);
+  float* Ulo = Klo + (size_t)m_cap * 4;
   (void)Ulo;
   (void)Llo;
   (void)Klo;
@@ -1271,20 +1273,21 @@ void fill_system_args(Args<TV>& A, const mka_system* s) {
 }
 
 // Dynamic shared memory of atoms_kernel: cluster list and local pattern, then the [m_cap][4]
-// work vectors of CG and the basis (three, and two low halves in the FP32 form), then
-// S_r - I of the four columns ([4][nu][nu] FP32).
-size_t dyn_smem_bytes(int nu, int lnnz_cap, int mcap, size_t elem) {
+// vector the SpMV gathers (p in CG, l in the basis; its low half too in the FP32 form).
+size_t dyn_smem_bytes(int lnnz_cap, int mcap, size_t elem) {
   size_t off = (size_t)(2 * kMaxCl + 1 + lnnz_cap) * sizeof(int) + (size_t)lnnz_cap * sizeof(uint16_t);
   off = align_up(off, 16);
-  return off + (size_t)(elem == 4 ? 5 : 3) * mcap * 4 * elem + sizeof(float) * 4 * (size_t)nu * nu;
+  return off + (size_t)mcap * 4 * elem + (elem == 4 ? (size_t)mcap * 4 * sizeof(float) : 0);
 }
 
 // Per-CTA global work slot: U and S U ([nu][m_cap][4]) and s_j ([m_cap][4]) in the arithmetic
-// type, then s_j in FP64 ([m_cap][4]), then (FP32 arithmetic) the low halves of the basis
-// vectors ([nu][m_cap][4] FP32).
+// type, then s_j in FP64 ([m_cap][4]), S_r - I of the four columns ([4][nu][nu] FP32), the two
+// streamed work vectors ([m_cap][4] each, arithmetic type), and (FP32 arithmetic) the low half
+// of H u ([m_cap][4]) and of the basis vectors ([nu][m_cap][4]).
 size_t slot_bytes_for(int nu, int mcap, size_t elem) {
   return align_up(elem * ((size_t)2 * nu + 1) * mcap * 4, 256) + align_up(sizeof(double) * 4 * (size_t)mcap, 256) +
-         (elem == 4 ? align_up(4 * (size_t)nu * mcap * 4, 256) : 0);
+         align_up(sizeof(float) * 4 * (size_t)nu * nu, 256) + elem * 2 * (size_t)mcap * 4 +
+         (elem == 4 ? 4 * ((size_t)nu + 1) * mcap * 4 : 0) + 256;
 }
 
 template <typename TV, typename T, int NT>
@@ -1293,7 +1296,7 @@ mka_status config_t(const mka_system* sys, int nu, int max_cl, int ctas_per_sm, 
   cf.threads = NT;
   cf.mcap = 4 * std::max(1, std::min(max_cl, kMaxCl));
   cf.lnnz_cap = std::max(1, std::min(max_cl, kMaxCl) * std::max(1, sys->max_row_blocks));
-  cf.smem = dyn_smem_bytes(nu, cf.lnnz_cap, cf.mcap, sizeof(T));
+  cf.smem = dyn_smem_bytes(cf.lnnz_cap, cf.mcap, sizeof(T));
   cf.slot_bytes = slot_bytes_for(nu, cf.mcap, sizeof(T));
   auto kern = atoms_kernel<TV, T, NT>;
   MKA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem));
