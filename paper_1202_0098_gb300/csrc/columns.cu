@@ -128,6 +128,7 @@ struct Args {
   size_t slot_bytes;
   int mcap;            // 4 x (largest cluster of the selection)
   int lnnz_cap;        // local-block capacity per cluster
+  int clcap;           // cluster list capacity (power of two)
   // outputs
   double* eps;
   double* w;
@@ -226,7 +227,7 @@ __device__ __forceinline__ int cell_coord(double x, double len, int n) {
 }
 
 // Atoms within R of atom a (minimum image) appended to cl via the shared counter;
-// returns the count (which may exceed kMaxCl: then nothing beyond kMaxCl is stored).
+// returns the count (which may exceed A.clcap: then nothing beyond A.clcap is stored).
 template <typename TV>
 __device__ int gather_cluster(const Args<TV>& A, int64_t a, int* cl, int* cnt) {
   if (threadIdx.x == 0) *cnt = 0;
@@ -247,7 +248,7 @@ __device__ int gather_cluster(const Args<TV>& A, int64_t a, int* cl, int* cnt) {
       const int b = A.cell_atoms[k];
       if (within_R(A.pos, A.posf, A.box, A.R2, A.pre_lo, A.pre_hi, b, px, py, pz, pxf, pyf, pzf)) {
         const int idx = atomicAdd(cnt, 1);
-        if (idx < kMaxCl) cl[idx] = b;
+        if (idx < A.clcap) cl[idx] = b;
       }
     }
   }
@@ -255,7 +256,7 @@ __device__ int gather_cluster(const Args<TV>& A, int64_t a, int* cl, int* cnt) {
   return *cnt;
 }
 
-// Ascending bitonic sort of cl[0..n) (n <= kMaxCl), padding with INT_MAX.
+// Ascending bitonic sort of cl[0..n) (n <= the list's power-of-two capacity), padding with INT_MAX.
 __device__ void sort_cluster(int* cl, int n) {
   int N = 2;
   while (N < n) N <<= 1;
@@ -300,17 +301,18 @@ __device__ __forceinline__ void st4(double* p, double a0, double a1, double a2, 
 // x, y are [m][4] in shared memory; other columns of y are left untouched.
 template <typename TV, typename T>
 __device__ __forceinline__ void spmm4(const TV* __restrict__ val, const int* lrow, const uint16_t* lcol,
-                                      const int* lblk, int ncl, const T* __restrict__ x, T* __restrict__ y,
+                                      const int* rbase, const uint8_t* loff, int ncl, const T* __restrict__ x, T* __restrict__ y,
                                       int mask) {
   const int m = 4 * ncl;
   for (int r = threadIdx.x; r < m; r += blockDim.x) {
     const int t = r >> 2, i = r & 3;
+    const int rb = rbase[t];
     T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     const int e1 = lrow[t + 1];
 #pragma unroll 4
     for (int e = lrow[t]; e < e1; ++e) {
       T v[4];
-      RowLoad<TV, T>::load(val, lblk[e], i, v);
+      RowLoad<TV, T>::load(val, rb + loff[e], i, v);
       const T* xb = x + (size_t)lcol[e] * 16;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -334,57 +336,19 @@ __device__ __forceinline__ void spmm4(const TV* __restrict__ val, const int* lro
   __syncthreads();
 }
 
-// r = e_j - A x for the four columns in FP32 with error-free products (FMA TwoProd) and
-// compensated sums (Knuth's TwoSum), so that the residual is accurate to a few rounding
-// errors of its own size rather than of |A| |x|. Explicit _rn operations keep the compiler
-// from contracting them.
-template <typename TV>
-__device__ void resid4_comp(const TV* __restrict__ val, const int* lrow, const uint16_t* lcol, const int* lblk,
-                            int ncl, const float* __restrict__ x, float* __restrict__ r, int jrow0) {
-  for (int row = threadIdx.x; row < 4 * ncl; row += blockDim.x) {
-    const int t = row >> 2, i = row & 3;
-    float hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
-    for (int e = lrow[t]; e < lrow[t + 1]; ++e) {
-      float v[4];
-      RowLoad<TV, float>::load(val, lblk[e], i, v);
-      const float* xb = x + (size_t)lcol[e] * 16;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        float xk[4];
-        ld4(xb + 4 * k, xk);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float p = __fmul_rn(v[k], xk[q]);
-          const float pe = fmaf(v[k], xk[q], -p);
-          const float s = __fadd_rn(hi[q], p);
-          const float bb = __fsub_rn(s, hi[q]);
-          const float err = __fadd_rn(__fsub_rn(hi[q], __fsub_rn(s, bb)), __fsub_rn(p, bb));
-          hi[q] = s;
-          lo[q] = __fadd_rn(lo[q], __fadd_rn(err, pe));
-        }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float e = (row == jrow0 + q) ? 1.0f : 0.0f;
-      r[4 * row + q] = __fsub_rn(__fsub_rn(e, hi[q]), lo[q]);
-    }
-  }
-  __syncthreads();
-}
-
 // r = e_j - A (hi + lo) for x given as an FP32 pair: the hi part with error-free products and
 // compensated sums as in resid4_comp, the small lo part (|lo| <= ulp(hi) / 2) in plain FP32.
 template <typename TV>
-__device__ void resid4_comp2(const TV* __restrict__ val, const int* lrow, const uint16_t* lcol, const int* lblk,
+__device__ void resid4_comp2(const TV* __restrict__ val, const int* lrow, const uint16_t* lcol, const int* rbase, const uint8_t* loff,
                              int ncl, const float* __restrict__ xh, const float* __restrict__ xl, float* __restrict__ r,
                              int jrow0) {
   for (int row = threadIdx.x; row < 4 * ncl; row += blockDim.x) {
     const int t = row >> 2, i = row & 3;
+    const int rb = rbase[t];
     float hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0}, sl[4] = {0, 0, 0, 0};
     for (int e = lrow[t]; e < lrow[t + 1]; ++e) {
       float v[4];
-      RowLoad<TV, float>::load(val, lblk[e], i, v);
+      RowLoad<TV, float>::load(val, rb + loff[e], i, v);
       const float* xb = xh + (size_t)lcol[e] * 16;
       const float* xc = xl + (size_t)lcol[e] * 16;
 #pragma unroll
@@ -419,16 +383,17 @@ __device__ void resid4_comp2(const TV* __restrict__ val, const int* lrow, const 
 // plain FP32, renormalised so that yh is the sum rounded to FP32 and |yl| <= ulp(yh) / 2
 // (yl == nullptr: yh only). Other columns are left untouched.
 template <typename TV>
-__device__ void spmm4_pair(const TV* __restrict__ val, const int* lrow, const uint16_t* lcol, const int* lblk,
+__device__ void spmm4_pair(const TV* __restrict__ val, const int* lrow, const uint16_t* lcol, const int* rbase, const uint8_t* loff,
                            int ncl, const float* __restrict__ xh, const float* __restrict__ xl, float* __restrict__ yh,
                            float* __restrict__ yl, int mask) {
   for (int row = threadIdx.x; row < 4 * ncl; row += blockDim.x) {
     const int t = row >> 2, i = row & 3;
+    const int rb = rbase[t];
     float hi[4] = {0, 0, 0, 0}, lo[4] = {0, 0, 0, 0};
     const int e1 = lrow[t + 1];
     for (int e = lrow[t]; e < e1; ++e) {
       float v[4];
-      RowLoad<TV, float>::load(val, lblk[e], i, v);
+      RowLoad<TV, float>::load(val, rb + loff[e], i, v);
       const float* xb = xh + (size_t)lcol[e] * 16;
       const float* xc = xl + (size_t)lcol[e] * 16;
 #pragma unroll
@@ -463,17 +428,18 @@ __device__ void spmm4_pair(const TV* __restrict__ val, const int* lrow, const ui
 // columns in `mask`; FP64 form.
 template <typename TV, typename T>
 __device__ void spmm4_hs(const TV* __restrict__ valH, const TV* __restrict__ valS, const int* lrow,
-                         const uint16_t* lcol, const int* lblk, int ncl, const T* __restrict__ x, T* __restrict__ yH,
+                         const uint16_t* lcol, const int* rbase, const uint8_t* loff, int ncl, const T* __restrict__ x, T* __restrict__ yH,
                          T* __restrict__ yS, int mask) {
   for (int r = threadIdx.x; r < 4 * ncl; r += blockDim.x) {
     const int t = r >> 2, i = r & 3;
+    const int rb = rbase[t];
     T h[4] = {0, 0, 0, 0}, s[4] = {0, 0, 0, 0};
     const int e1 = lrow[t + 1];
 #pragma unroll 2
     for (int e = lrow[t]; e < e1; ++e) {
       T vh[4], vs[4];
-      RowLoad<TV, T>::load(valH, lblk[e], i, vh);
-      RowLoad<TV, T>::load(valS, lblk[e], i, vs);
+      RowLoad<TV, T>::load(valH, rb + loff[e], i, vh);
+      RowLoad<TV, T>::load(valS, rb + loff[e], i, vs);
       const T* xb = x + (size_t)lcol[e] * 16;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -501,17 +467,18 @@ __device__ void spmm4_hs(const TV* __restrict__ valH, const TV* __restrict__ val
 // part (S u enters the coefficients, whose errors stay in the span, and S_r, unmagnified).
 template <typename TV>
 __device__ void spmm4_pair_hs(const TV* __restrict__ valH, const TV* __restrict__ valS, const int* lrow,
-                              const uint16_t* lcol, const int* lblk, int ncl, const float* __restrict__ xh,
+                              const uint16_t* lcol, const int* rbase, const uint8_t* loff, int ncl, const float* __restrict__ xh,
                               const float* __restrict__ xl, float* __restrict__ yHh, float* __restrict__ yHl,
                               float* __restrict__ yS, int mask) {
   for (int row = threadIdx.x; row < 4 * ncl; row += blockDim.x) {
     const int t = row >> 2, i = row & 3;
+    const int rb = rbase[t];
     float hh[4] = {0, 0, 0, 0}, hl[4] = {0, 0, 0, 0}, sh[4] = {0, 0, 0, 0};
     const int e1 = lrow[t + 1];
     for (int e = lrow[t]; e < e1; ++e) {
       float vh[4], vs[4];
-      RowLoad<TV, float>::load(valH, lblk[e], i, vh);
-      RowLoad<TV, float>::load(valS, lblk[e], i, vs);
+      RowLoad<TV, float>::load(valH, rb + loff[e], i, vh);
+      RowLoad<TV, float>::load(valS, rb + loff[e], i, vs);
       const float* xb = xh + (size_t)lcol[e] * 16;
       const float* xc = xl + (size_t)lcol[e] * 16;
 #pragma unroll
@@ -636,19 +603,20 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
   __shared__ AtomState st;
   __shared__ double red[2 * kMaxWarps * 4];
   __shared__ double sums[4];
-  __shared__ double coef[MKA_MAX_NU * 4];
-  __shared__ T coefT[MKA_MAX_NU * 4];    // the same coefficients in the arithmetic type
   __shared__ T scal[12];                 // CG alpha [0..4), CG beta [4..8), 1 / beta of the basis [8..12)
   __shared__ int64_t cur_atom;
   __shared__ int cnt;
 
   const int nu = A.nu;
   const int m_cap = A.mcap;
-  int* cl = reinterpret_cast<int*>(smem_raw);                            // kMaxCl
-  int* lrow = cl + kMaxCl;                                                // kMaxCl + 1
-  int* lblk = lrow + kMaxCl + 1;                                          // lnnz_cap
-  uint16_t* lcol = reinterpret_cast<uint16_t*>(lblk + A.lnnz_cap);        // lnnz_cap
-  size_t off = (size_t)(2 * kMaxCl + 1 + A.lnnz_cap) * sizeof(int) + (size_t)A.lnnz_cap * sizeof(uint16_t);
+  // cluster list, local row pointers and each local row's first global block; then per local
+  // block its local column and its offset within the global row
+  int* cl = reinterpret_cast<int*>(smem_raw);                            // clcap
+  int* lrow = cl + A.clcap;                                               // clcap + 1
+  int* rbase = lrow + A.clcap + 1;                                        // clcap
+  uint16_t* lcol = reinterpret_cast<uint16_t*>(rbase + A.clcap);          // lnnz_cap
+  uint8_t* loff = reinterpret_cast<uint8_t*>(lcol + A.lnnz_cap);          // lnnz_cap
+  size_t off = (size_t)(3 * A.clcap + 1) * sizeof(int) + (size_t)A.lnnz_cap * (sizeof(uint16_t) + 1);
   off = (off + 15) & ~(size_t)15;
   // Shared memory holds the vector the SpMV gathers through the cluster pattern; the vectors
   // that are only streamed row by row live in the CTA's global slot.
@@ -656,6 +624,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
   T* V0 = reinterpret_cast<T*>(region);     // CG: p     basis: l
   // FP32 form only: the low half of l
   float* Llo = reinterpret_cast<float*>(V0 + (size_t)m_cap * 4);
+  // Gram-Schmidt coefficients [nu][4] in FP64 and in the arithmetic type
+  double* coef = reinterpret_cast<double*>(region + (size_t)m_cap * 4 * (sizeof(T) + (sizeof(T) == 4 ? 4 : 0)));
+  T* coefT = reinterpret_cast<T*>(coef + (size_t)nu * 4);
 
   char* slot = A.scratch + (size_t)blockIdx.x * A.slot_bytes;
   T* U = reinterpret_cast<T*>(slot);                 // [nu][m_cap][4]
@@ -686,7 +657,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
 
     // ---- 1. cluster ----------------------------------------------------------------
     const int ncl_raw = gather_cluster(A, atom, cl, &cnt);
-    if (ncl_raw > kMaxCl || 4 * ncl_raw > m_cap) {
+    if (ncl_raw > A.clcap || 4 * ncl_raw > m_cap) {
       for (int c = threadIdx.x; c < 4; c += blockDim.x) {   // the reduced pass writes zero outputs
         const int64_t col = 4 * widx + c;
         A.status[col] = ST_TOOLARGE;
@@ -734,12 +705,14 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
     }
     for (int t = threadIdx.x; t < ncl; t += blockDim.x) {
       const int b = cl[t];
+      const int k0 = A.row_ptr[b];
       int e = lrow[t];
-      for (int k = A.row_ptr[b]; k < A.row_ptr[b + 1]; ++k) {
+      rbase[t] = k0;
+      for (int k = k0; k < A.row_ptr[b + 1]; ++k) {   // rows hold at most 255 blocks (checked at setup)
         const int lc = find_local(cl, ncl, A.col[k]);
         if (lc >= 0) {
           lcol[e] = (uint16_t)lc;
-          lblk[e] = k;
+          loff[e] = (uint8_t)(k - k0);
           ++e;
         }
       }
@@ -773,7 +746,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
         P[4 * (4 * lk + o) + c] = v;
       }
       __syncthreads();
-      spmm4<TV, T>(A.valS, lrow, lcol, lblk, ncl, P, AP, 15);
+      spmm4<TV, T>(A.valS, lrow, lcol, rbase, loff, ncl, P, AP, 15);
       for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
         const int r = i >> 2, c = i & 3;
         R[i] = ((r == 4 * t0 + c) ? (T)1 : (T)0) - AP[i];
@@ -832,7 +805,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
         }
         __syncthreads();
         if constexpr (sizeof(T) == 4)
-          resid4_comp2<TV>(A.valS, lrow, lcol, lblk, ncl, reinterpret_cast<const float*>(P),
+          resid4_comp2<TV>(A.valS, lrow, lcol, rbase, loff, ncl, reinterpret_cast<const float*>(P),
                            reinterpret_cast<const float*>(AP), reinterpret_cast<float*>(R), 4 * t0);
         dot4<T>(R, R, m, red, sums);
         if (threadIdx.x < 4) {
@@ -848,7 +821,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
       for (int it = 0; it < maxit; ++it) {
         const int cmask = st.cg_active[0] | (st.cg_active[1] << 1) | (st.cg_active[2] << 2) | (st.cg_active[3] << 3);
         if (!cmask) break;
-        spmm4<TV, T>(A.valS, lrow, lcol, lblk, ncl, P, AP, cmask);
+        spmm4<TV, T>(A.valS, lrow, lcol, rbase, loff, ncl, P, AP, cmask);
         dot4<T>(P, AP, m, red, sums);
         if (threadIdx.x < 4) {
           const int c = threadIdx.x;
@@ -1062,9 +1035,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
       // pair from the pair, S l in FP32.
       // KV held H u of the last accepted vector, whose projection the sweep above has taken.
       if constexpr (sizeof(T) == 4)
-        spmm4_pair_hs<TV>(A.valH, A.valS, lrow, lcol, lblk, ncl, Lv, Llo, KV, Klo, SL, amask);
+        spmm4_pair_hs<TV>(A.valH, A.valS, lrow, lcol, rbase, loff, ncl, Lv, Llo, KV, Klo, SL, amask);
       else
-        spmm4_hs<TV, T>(A.valH, A.valS, lrow, lcol, lblk, ncl, Lv, KV, SL, amask);
+        spmm4_hs<TV, T>(A.valH, A.valS, lrow, lcol, rbase, loff, ncl, Lv, KV, SL, amask);
       dot4<T>(Lv, SL, m, red, sums);
       if (threadIdx.x < 4) {
         const int c = threadIdx.x;
@@ -1155,9 +1128,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
         }
         __syncthreads();
         if constexpr (sizeof(T) == 4)
-          spmm4_pair<TV>(A.valH, lrow, lcol, lblk, ncl, Lv, Llo, KV, Klo, kmask);
+          spmm4_pair<TV>(A.valH, lrow, lcol, rbase, loff, ncl, Lv, Llo, KV, Klo, kmask);
         else
-          spmm4<TV, T>(A.valH, lrow, lcol, lblk, ncl, Lv, KV, kmask);
+          spmm4<TV, T>(A.valH, lrow, lcol, rbase, loff, ncl, Lv, KV, kmask);
       }
       for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
         const int c = i & 3;
@@ -1206,7 +1179,6 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
     }
     if (A.keep) {
       // pattern rows of U (zero outside the cluster): rho_ij = U_i . (C diag(f) V_j)
-      const int64_t rbase = A.row_ptr[atom];
       const int nrow = A.row_ptr[atom + 1] - A.row_ptr[atom];
       double* vpa = A.vp + A.blk_off[widx] * 16 * (int64_t)nu;
       for (int i = threadIdx.x; i < nrow * 16 * nu; i += blockDim.x) vpa[i] = 0.0;
@@ -1215,7 +1187,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
       for (int i = threadIdx.x; i < 16 * ne * nu; i += blockDim.x) {
         const int n = i % nu, rem = i / nu, c = rem / (4 * ne), er = rem % (4 * ne), e = e0 + er / 4, r = er % 4;
         if (n >= st.n[c]) continue;
-        const int k = (int)(lblk[e] - rbase);
+        const int k = loff[e];   // the atom's own row: offset = block index within the row
         vpa[((int64_t)k * 16 + c * 4 + r) * nu + n] = (double)U[(size_t)n * m_cap * 4 + 4 * (4 * (int)lcol[e] + r) + c];
       }
     }
@@ -1273,11 +1245,13 @@ void fill_system_args(Args<TV>& A, const mka_system* s) {
 }
 
 // Dynamic shared memory of atoms_kernel: cluster list and local pattern, then the [m_cap][4]
-// vector the SpMV gathers (p in CG, l in the basis; its low half too in the FP32 form).
-size_t dyn_smem_bytes(int lnnz_cap, int mcap, size_t elem) {
-  size_t off = (size_t)(2 * kMaxCl + 1 + lnnz_cap) * sizeof(int) + (size_t)lnnz_cap * sizeof(uint16_t);
+// vector the SpMV gathers (p in CG, l in the basis; its low half too in the FP32 form), then
+// the Gram-Schmidt coefficients ([nu][4] in FP64 and in the arithmetic type).
+size_t dyn_smem_bytes(int nu, int clcap, int lnnz_cap, int mcap, size_t elem) {
+  size_t off = (size_t)(3 * clcap + 1) * sizeof(int) + (size_t)lnnz_cap * (sizeof(uint16_t) + 1);
   off = align_up(off, 16);
-  return off + (size_t)mcap * 4 * elem + (elem == 4 ? (size_t)mcap * 4 * sizeof(float) : 0);
+  return off + (size_t)mcap * 4 * elem + (elem == 4 ? (size_t)mcap * 4 * sizeof(float) : 0) +
+         (size_t)nu * 4 * (sizeof(double) + elem);
 }
 
 // Per-CTA global work slot: U and S U ([nu][m_cap][4]) and s_j ([m_cap][4]) in the arithmetic
@@ -1294,9 +1268,14 @@ template <typename TV, typename T, int NT>
 mka_status config_t(const mka_system* sys, int nu, int max_cl, int ctas_per_sm, AtomsConfig* out) {
   AtomsConfig cf{};
   cf.threads = NT;
-  cf.mcap = 4 * std::max(1, std::min(max_cl, kMaxCl));
-  cf.lnnz_cap = std::max(1, std::min(max_cl, kMaxCl) * std::max(1, sys->max_row_blocks));
-  cf.smem = dyn_smem_bytes(cf.lnnz_cap, cf.mcap, sizeof(T));
+  if (sys->max_row_blocks > 255)
+    return fail(MKA_ERR_INVALID_ARG, "rows of more than 255 blocks are not supported by the per-atom kernel");
+  const int cl_atoms = std::max(1, std::min(max_cl, kMaxCl));
+  cf.mcap = 4 * cl_atoms;
+  cf.lnnz_cap = cl_atoms * std::max(1, sys->max_row_blocks);
+  cf.clcap = 2;
+  while (cf.clcap < cl_atoms) cf.clcap <<= 1;
+  cf.smem = dyn_smem_bytes(nu, cf.clcap, cf.lnnz_cap, cf.mcap, sizeof(T));
   cf.slot_bytes = slot_bytes_for(nu, cf.mcap, sizeof(T));
   auto kern = atoms_kernel<TV, T, NT>;
   MKA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cf.smem));
@@ -1330,6 +1309,7 @@ mka_status launch_t(const mka_system* sys, const AtomsConfig& cf, const AtomsLau
   A.slot_bytes = cf.slot_bytes;
   A.mcap = cf.mcap;
   A.lnnz_cap = cf.lnnz_cap;
+  A.clcap = cf.clcap;
   A.eps = a.eps;
   A.w = a.w;
   A.nu_eff = a.nu_eff;

@@ -89,6 +89,7 @@ struct AtomsConfig {
   size_t slot_bytes = 0;   // global work slot per CTA
   int mcap = 0;            // 4 x largest cluster
   int lnnz_cap = 0;        // local block capacity
+  int clcap = 0;           // cluster list capacity: the power of two at or above the largest cluster
 };
 
 // Arguments of one launch of the per-atom kernel over a selection.
