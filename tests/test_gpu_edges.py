@@ -1,0 +1,124 @@
+"""Edge cases of the CUDA path through the C ABI, against the FP64 oracle.
+
+* the largest subspace the library accepts (nu = MKA_MAX_NU = 64, p = q = 32);
+* an atom listed twice in one selection (its columns are independent of the rest, so both
+  copies equal each other and the oracle);
+* a cluster larger than the declared cap (the allocation-free entry point with
+  max_cluster_atoms below the real cluster size): every column reports
+  MKA_ERR_CLUSTER_TOO_LARGE with zero outputs, and the call itself succeeds;
+* empty selections, rejected before any device work.
+"""
+import numpy as np
+import pytest
+
+from oracle import system as osys
+from oracle.parallel import solve_atoms_parallel
+from synth import SK_CARBON_LIKE, lattice_positions
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1202_0098_gb300 import build, mka
+    build.build()
+    mka.load()
+    return mka
+
+
+@pytest.fixture(scope="module")
+def system(lib):
+    pos, box = lattice_positions("diamond", 3.567, 3, 0.08, 0.0, 13)
+    s = lib.mka_build_system(pos, box, SK_CARBON_LIKE, "fp64", cluster_radius=5.0)
+    yield pos, box, s
+    lib.mka_system_destroy(s)
+
+
+def solve(mka, s, atoms, p, q):
+    res = mka.mka_solve_columns(s, atoms, mka.solve_params(p, q, cg_tol=1e-13, keep_vectors=True))
+    return res, mka.mka_result_copy_levels(res)
+
+
+def density(mka, s, res, mu, kT):
+    nb = mka.mka_result_info(res)["n_blocks"]
+    rho = torch.empty(nb * 16, dtype=torch.float64, device="cuda")
+    e, _ = mka.mka_density_energy(s, res, mu, kT, rho.data_ptr())
+    return rho.cpu().numpy().reshape(nb, 4, 4), e
+
+
+def test_largest_subspace(lib, system):
+    mka = lib
+    pos, box, s = system
+    atoms = np.array([3, 77, 150], dtype=np.int64)
+    p = q = mka.MKA_MAX_NU // 2
+    ores = solve_atoms_parallel(pos, box, SK_CARBON_LIKE, 5.0, atoms, p, q)
+    res, lv = solve(mka, s, atoms, p, q)
+    try:
+        oe, ow = osys.stack_eps_w(ores)
+        np.testing.assert_array_equal(lv["nu_eff"], [c.nu_eff for r in ores for c in r.data])
+        np.testing.assert_allclose(lv["eps"], oe, rtol=0, atol=TOL)
+        np.testing.assert_allclose(lv["w"], ow, rtol=0, atol=TOL)
+        rho, e = density(mka, s, res, 0.3, 0.1)
+        orho, oe_band, _ = osys.density(ores, 0.3, 0.1)
+        np.testing.assert_allclose(rho, np.concatenate(orho), rtol=0, atol=TOL)
+        assert abs(e - oe_band) / len(atoms) < TOL
+    finally:
+        mka.mka_result_destroy(res)
+
+
+def test_repeated_atom(lib, system):
+    mka = lib
+    pos, box, s = system
+    atoms = np.array([40, 9, 40], dtype=np.int64)
+    res, lv = solve(mka, s, atoms, 8, 8)
+    try:
+        for key in ("eps", "w", "nu_eff", "status", "cg_iters"):
+            np.testing.assert_array_equal(lv[key][0:4], lv[key][8:12])
+        ores = solve_atoms_parallel(pos, box, SK_CARBON_LIKE, 5.0, atoms[:1], 8, 8)
+        oe, ow = osys.stack_eps_w(ores)
+        np.testing.assert_allclose(lv["eps"][8:12], oe, rtol=0, atol=TOL)
+        rho, _ = density(mka, s, res, 0.3, 0.1)
+        rp = mka.mka_system_copy_bsr(s, values=False)["row_ptr"]
+        nrow = int(rp[41] - rp[40])                       # blocks of atom 40's row
+        np.testing.assert_array_equal(rho[:nrow], rho[-nrow:])
+    finally:
+        mka.mka_result_destroy(res)
+
+
+def test_cluster_beyond_the_declared_cap(lib, system):
+    mka = lib
+    pos, box, s = system
+    atoms = np.array([0, 100], dtype=np.int64)
+    assert int(mka.mka_cluster_sizes(s, atoms).min()) > 10
+    n, nu = 4 * len(atoms), 16
+    eps = torch.full((n, nu), float("nan"), dtype=torch.float64, device="cuda")
+    w = torch.full((n, nu), float("nan"), dtype=torch.float64, device="cuda")
+    ib = [torch.full((n,), -1, dtype=torch.int32, device="cuda") for _ in range(3)]
+    mka.mka_solve_columns_static(s, atoms, 8, 8, 1e-12, 500, 10, eps.data_ptr(), w.data_ptr(), ib[0].data_ptr(),
+                                 ib[1].data_ptr(), ib[2].data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert np.all(ib[2].cpu().numpy() == mka.MKA_ERR_CLUSTER_TOO_LARGE)
+    assert np.all(ib[0].cpu().numpy() == 0)
+    assert np.all(eps.cpu().numpy() == 0.0) and np.all(w.cpu().numpy() == 0.0)
+
+
+def test_empty_selections_are_rejected(lib, system):
+    mka = lib
+    _, _, s = system
+    none = np.zeros(0, dtype=np.int64)
+    with pytest.raises(mka.MkaError) as e:
+        mka.mka_solve_columns(s, none, mka.solve_params(8, 8))
+    assert e.value.status == mka.MKA_ERR_INVALID_ARG
+    with pytest.raises(mka.MkaError) as e:
+        mka.mka_cluster_sizes(s, none)
+    assert e.value.status == mka.MKA_ERR_INVALID_ARG
+    plan = mka.mka_plan_create(s, 8, mka.solve_params(8, 8, keep_vectors=True))
+    try:
+        with pytest.raises(mka.MkaError) as e:
+            mka.mka_plan_run(plan, none, 0.0, 0.1)
+        assert e.value.status == mka.MKA_ERR_INVALID_ARG
+    finally:
+        mka.mka_plan_destroy(plan)
