@@ -186,7 +186,7 @@ mka_status mka_solve_columns(mka_system* sys, const int64_t* atoms, int64_t n_se
  *   nu_eff, cg_iters, status  int32 [4 n_sel] (status: a mka_status value;
  *               MKA_ERR_CLUSTER_TOO_LARGE when an atom's cluster has more
  *               than `max_cluster_atoms` atoms)
- * Pattern rows of v_alpha are not kept (no rho / G from this call).
+ * Nothing for rho / G is kept (keep_vectors = 0 in effect).
  * Work memory (the work-queue counter, the atom list of a chunk, the chunk's
  * reduced problems, 8 (2 nu^2 + 2 nu) bytes per column, and one work slot per
  * CTA of about 8 (2 (p+q) + 2) x 4 max_cluster_atoms x 4 bytes) comes from one
