@@ -6,7 +6,8 @@
 * a cluster larger than the declared cap (the allocation-free entry point with
   max_cluster_atoms below the real cluster size): every column reports
   MKA_ERR_CLUSTER_TOO_LARGE with zero outputs, and the call itself succeeds;
-* empty selections, rejected before any device work.
+* empty selections, rejected before any device work;
+* the p_x / p_y columns of a z-axis dimer against the closed form of their 2x2 pencil.
 """
 import numpy as np
 import pytest
@@ -122,3 +123,32 @@ def test_empty_selections_are_rejected(lib, system):
         assert e.value.status == mka.MKA_ERR_INVALID_ARG
     finally:
         mka.mka_plan_destroy(plan)
+
+
+def test_pi_dimer_closed_form(lib):
+    """The p_x / p_y columns of a z-axis dimer against the closed form of their 2x2 pencil
+    (levels (Ep +- V) / (1 +- s), weights 1/2; see the oracle's pin of the same case)."""
+    mka = lib
+    from synth import SK_CARBON_LIKE as sk
+    pos = np.array([[5.0, 5.0, 5.0], [5.0, 5.0, 5.0 + sk.d0]])
+    box = np.array([20.0, 20.0, 20.0])
+    V, s_ = sk.V[3], sk.Sv[3]
+    levels = np.sort([(sk.Ep + V) / (1 + s_), (sk.Ep - V) / (1 - s_)])
+    mu, kT = 1.0, 0.1
+    f = lambda e: 1.0 / (1.0 + np.exp((e - mu) / kT))
+    fb, fa = f((sk.Ep + V) / (1 + s_)), f((sk.Ep - V) / (1 - s_))
+    same, other = fb / (2 * (1 + s_)) + fa / (2 * (1 - s_)), fb / (2 * (1 + s_)) - fa / (2 * (1 - s_))
+    s = mka.mka_build_system(pos, box, sk, "fp64", cluster_radius=3.0)
+    try:
+        res, lv = solve(mka, s, np.array([0], dtype=np.int64), 2, 2)
+        try:
+            rho, _ = density(mka, s, res, mu, kT)            # atom 0's row: blocks (atom 0, atom 1)
+            for o in (1, 2):
+                assert lv["nu_eff"][o] == 2
+                np.testing.assert_allclose(lv["eps"][o][:2], levels, rtol=0, atol=TOL)
+                np.testing.assert_allclose(lv["w"][o][:2], [0.5, 0.5], rtol=0, atol=TOL)
+                assert abs(rho[0, o, o] - same) < TOL and abs(rho[1, o, o] - other) < TOL
+        finally:
+            mka.mka_result_destroy(res)
+    finally:
+        mka.mka_system_destroy(s)

@@ -233,3 +233,40 @@ def test_fermi_function():
     x = np.linspace(-2, 2, 41)
     np.testing.assert_allclose(mka.fermi(x, 0.1, 0.2), 1.0 / (1.0 + np.exp((x - 0.1) / 0.2)), rtol=0, atol=1e-15)
     assert mka.fermi(-1e4, 0.0, 0.1) == 1.0 and mka.fermi(1e4, 0.0, 0.1) == 0.0
+
+
+def _pi_dimer():
+    """Two atoms on the z axis at the reference bond length in a large box."""
+    from synth import SK_CARBON_LIKE
+    pos = np.array([[5.0, 5.0, 5.0], [5.0, 5.0, 5.0 + SK_CARBON_LIKE.d0]])
+    return pos, np.array([20.0, 20.0, 20.0]), SK_CARBON_LIKE
+
+
+def _pi_dimer_closed_form(sk, mu, kT):
+    """The p_x (or p_y) orbitals of a z-axis dimer see only the pp-pi couplings (direction cosine 0):
+    the 2x2 pencil H = [[Ep, V], [V, Ep]], S = [[1, s], [s, 1]] with V = pp-pi of H, s = pp-pi of S
+    at the reference length. Its eigenvectors are (1, +-1) / sqrt(2 (1 +- s)), so the levels are
+    (Ep +- V) / (1 +- s), both with weight 1/2, and rho_{j'j} = f_+ / (2 (1 + s)) +- f_- / (2 (1 - s))
+    for j' = j and for j' the same orbital on the other atom."""
+    V, s = sk.V[3], sk.Sv[3]
+    e_plus, e_minus = (sk.Ep + V) / (1 + s), (sk.Ep - V) / (1 - s)
+    f = lambda e: 1.0 / (1.0 + np.exp((e - mu) / kT))
+    same = f(e_plus) / (2 * (1 + s)) + f(e_minus) / (2 * (1 - s))
+    other = f(e_plus) / (2 * (1 + s)) - f(e_minus) / (2 * (1 - s))
+    return np.sort([e_plus, e_minus]), same, other
+
+
+def test_pi_dimer_closed_form():
+    pos, box, sk = _pi_dimer()
+    mu, kT = 1.0, 0.1
+    levels, same, other = _pi_dimer_closed_form(sk, mu, kT)
+    res = system.solve_atom(pos, box, sk, 3.0, 0, 2, 2)
+    rho, _, _ = system.density([res], mu, kT)
+    for o in (1, 2):                                     # p_x and p_y columns of atom 0
+        c = res.data[o]
+        assert c.nu_eff == 2                             # the pi block is invariant: the basis closes
+        np.testing.assert_allclose(c.eps, levels, rtol=0, atol=1e-13)
+        np.testing.assert_allclose(c.w, [0.5, 0.5], rtol=0, atol=1e-13)
+        k_self, k_other = list(res.neigh).index(0), list(res.neigh).index(1)
+        assert abs(rho[0][k_self, o, o] - same) < 1e-13
+        assert abs(rho[0][k_other, o, o] - other) < 1e-13
