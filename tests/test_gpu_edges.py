@@ -7,7 +7,8 @@
   max_cluster_atoms below the real cluster size): every column reports
   MKA_ERR_CLUSTER_TOO_LARGE with zero outputs, and the call itself succeeds;
 * empty selections, rejected before any device work;
-* the p_x / p_y columns of a z-axis dimer against the closed form of their 2x2 pencil.
+* the p_x / p_y columns of a z-axis dimer against the closed form of their 2x2 pencil;
+* a single-atom cluster against its on-site block.
 """
 import numpy as np
 import pytest
@@ -148,6 +149,36 @@ def test_pi_dimer_closed_form(lib):
                 np.testing.assert_allclose(lv["eps"][o][:2], levels, rtol=0, atol=TOL)
                 np.testing.assert_allclose(lv["w"][o][:2], [0.5, 0.5], rtol=0, atol=TOL)
                 assert abs(rho[0, o, o] - same) < TOL and abs(rho[1, o, o] - other) < TOL
+        finally:
+            mka.mka_result_destroy(res)
+    finally:
+        mka.mka_system_destroy(s)
+
+
+def test_single_atom_cluster(lib):
+    """R below the bond length (the oracle pins the same case against the on-site block): one level
+    per column, the on-site energy with weight 1; rho is its Fermi factor on the diagonal of the
+    atom's own block and zero in the blocks of the pattern atoms outside the cluster."""
+    mka = lib
+    from synth import SK_CARBON_LIKE as sk
+    pos, box = lattice_positions("diamond", 3.567, 3, 0.05, 0.0, 3)
+    mu, kT = 0.5, 0.1
+    s = mka.mka_build_system(pos, box, sk, "fp64", cluster_radius=1.0)
+    try:
+        atoms = np.array([7], dtype=np.int64)
+        assert int(mka.mka_cluster_sizes(s, atoms)[0]) == 1
+        res, lv = solve(mka, s, atoms, 3, 3)
+        try:
+            rho, _ = density(mka, s, res, mu, kT)
+            rp = mka.mka_system_copy_bsr(s, values=False)
+            row = list(rp["col"][rp["row_ptr"][7]:rp["row_ptr"][8]])
+            onsite = [sk.Es, sk.Ep, sk.Ep, sk.Ep]
+            expect = np.zeros_like(rho)
+            for o in range(4):
+                assert lv["nu_eff"][o] == 1
+                assert abs(lv["eps"][o][0] - onsite[o]) < TOL and abs(lv["w"][o][0] - 1.0) < TOL
+                expect[row.index(7), o, o] = 1.0 / (1.0 + np.exp((onsite[o] - mu) / kT))
+            np.testing.assert_allclose(rho, expect, rtol=0, atol=TOL)
         finally:
             mka.mka_result_destroy(res)
     finally:

@@ -270,3 +270,25 @@ def test_pi_dimer_closed_form():
         k_self, k_other = list(res.neigh).index(0), list(res.neigh).index(1)
         assert abs(rho[0][k_self, o, o] - same) < 1e-13
         assert abs(rho[0][k_other, o, o] - other) < 1e-13
+
+
+def test_single_atom_cluster():
+    """R below the bond length: the cluster is the atom alone, H_c = diag(Es, Ep, Ep, Ep), S_c = I.
+    Every column closes at nu_eff = 1 (s_j = e_j is already in the span) with its on-site level and
+    weight 1; rho is f of that level on the diagonal and zero elsewhere, the pattern atoms outside
+    the cluster included (reading A16)."""
+    from synth import SK_CARBON_LIKE as sk
+    pos, box = lattice_positions("diamond", 3.567, 3, 0.05, 0.0, 3)
+    mu, kT = 0.5, 0.1
+    res = system.solve_atom(pos, box, sk, 1.0, 7, 3, 3)
+    assert list(res.cluster) == [7] and len(res.neigh) > 1
+    rho, _, _ = system.density([res], mu, kT)
+    onsite = [sk.Es, sk.Ep, sk.Ep, sk.Ep]
+    k_self = list(res.neigh).index(7)
+    expect = np.zeros_like(rho[0])
+    for o in range(4):
+        c = res.data[o]
+        assert c.nu_eff == 1
+        assert abs(c.eps[0] - onsite[o]) < 1e-14 and abs(c.w[0] - 1.0) < 1e-14
+        expect[k_self, o, o] = 1.0 / (1.0 + np.exp((onsite[o] - mu) / kT))
+    np.testing.assert_allclose(rho[0], expect, rtol=0, atol=1e-14)
