@@ -292,3 +292,86 @@ def test_single_atom_cluster():
         assert abs(c.eps[0] - onsite[o]) < 1e-14 and abs(c.w[0] - 1.0) < 1e-14
         expect[k_self, o, o] = 1.0 / (1.0 + np.exp((onsite[o] - mu) / kT))
     np.testing.assert_allclose(rho[0], expect, rtol=0, atol=1e-14)
+
+
+def _s_projector(H, S, j, p):
+    """Pi_p = Q (Q^T S Q)^{-1} Q^T S: the S-orthogonal projector onto K_p(H; e_j), from an explicit,
+    Euclidean-QR-orthonormalised Krylov matrix (no S-orthogonalisation, no Gram-Schmidt of the oracle)."""
+    m = H.shape[0]
+    e = np.zeros(m)
+    e[j] = 1.0
+    cols = [e]
+    for _ in range(p - 1):
+        v = H @ cols[-1]
+        cols.append(v / np.linalg.norm(v))
+    Q, _ = np.linalg.qr(np.array(cols).T)
+    return Q @ np.linalg.solve(Q.T @ S @ Q, Q.T @ S), Q
+
+
+def reading_a_subspace(H, S, j, p, q):
+    """Closed form of the seam reading for any q: L = K_p(H; e_j) (+) K_q(H_hat; t) with
+    t = (I - Pi_p) s_j and H_hat = (I - Pi_p) H. Every vector the second chain adds is S-orthogonal
+    to K_p(H; e_j), so H acting on it leaves that space only through its Pi_p part, which lies in the
+    span already; hence the recursion of Eqs. EQ-KN-HUN / EQ-CALC-S-INV spans exactly this sum."""
+    m = H.shape[0]
+    Pi, Q = _s_projector(H, S, j, p)
+    e = np.zeros(m)
+    e[j] = 1.0
+    t = np.linalg.solve(S, e)
+    t = t - Pi @ t
+    T = [t / np.linalg.norm(t)]
+    for _ in range(q - 1):
+        v = H @ T[-1]
+        v = v - Pi @ v
+        T.append(v / np.linalg.norm(v))
+    return np.hstack([Q, np.array(T).T])
+
+
+def reading_b_subspace(H, S, j, p, q):
+    """The literal direct sum K_p(H; e_j) + K_q(H; s_j): a separate chain on s_j."""
+    m = H.shape[0]
+    _, Q = _s_projector(H, S, j, p)
+    e = np.zeros(m)
+    e[j] = 1.0
+    s = np.linalg.solve(S, e)
+    T = [s / np.linalg.norm(s)]
+    for _ in range(q - 1):
+        v = H @ T[-1]
+        T.append(v / np.linalg.norm(v))
+    return np.hstack([Q, np.array(T).T])
+
+
+@pytest.mark.parametrize("p,q,seed", [(3, 2, 41), (4, 3, 42), (5, 5, 43), (6, 4, 44)])
+def test_second_chain_closed_form(p, q, seed):
+    """q >= 2: the oracle's seam recursion spans K_p(H; e_j) (+) K_q((I - Pi_p) H; (I - Pi_p) s_j),
+    built here from explicit Krylov matrices and the S-projector formula. rho, G and the Ritz levels
+    of the Galerkin problem on that span match the oracle; the literal direct sum (a second chain on
+    s_j itself) does not, so the pin tells the two readings apart."""
+    m = 40
+    H, S = random_symmetric_pair(m, seed)
+    j, mu, kT, z = 5, 0.1, 0.25, 0.3 + 0.4j
+    col = mka.solve_column(H, S, j, p, q)
+    assert col.basis.nu_eff == p + q
+    W = reading_a_subspace(H, S, j, p, q)
+    Qw, _ = np.linalg.qr(W)
+    e, Y = scipy.linalg.eigh(Qw.T @ H @ Qw, Qw.T @ S @ Qw)
+    Vg = Qw @ Y
+    rows = np.arange(m)
+    f = mka.fermi(col.eps, mu, kT)
+    np.testing.assert_allclose(col.eps, e, atol=1e-10)
+    np.testing.assert_allclose(mka.rho_column(col, f, rows), Vg @ (mka.fermi(e, mu, kT) * Vg[j, :]), atol=1e-10)
+    np.testing.assert_allclose(mka.greens_column(col, z, rows), Vg @ (Vg[j, :] / (z - e)), atol=1e-10)
+    rho_b = galerkin_rho(H, S, reading_b_subspace(H, S, j, p, q), j, mu, kT)
+    assert np.abs(mka.rho_column(col, f, rows) - rho_b).max() > 1e-6
+
+
+def test_second_chain_pin_catches_h_on_s():
+    """A plausible slip in the seam recursion (H acting on s_j instead of on u_{p+1}) is caught by the
+    closed form: the planted variant builds the reading-B span and misses it by far more than 1e-10."""
+    m, p, q, j = 40, 4, 3, 5
+    H, S = random_symmetric_pair(m, 45)
+    mu, kT = 0.1, 0.25
+    W = reading_a_subspace(H, S, j, p, q)
+    ref = galerkin_rho(H, S, W, j, mu, kT)
+    planted = galerkin_rho(H, S, reading_b_subspace(H, S, j, p, q), j, mu, kT)
+    assert np.abs(planted - ref).max() > 1e-6

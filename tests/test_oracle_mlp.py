@@ -59,3 +59,55 @@ def test_features_on_perfect_diamond():
     np.testing.assert_allclose(np.linalg.norm(geo[:28, 1:], axis=1), 1.0, atol=1e-12)
     assert patch[0] == 0 and len(set(patch.tolist())) == 17
     np.testing.assert_array_equal(X[:, 128:], np.eye(4))
+
+
+def test_silu_closed_values():
+    """SiLU(x) = x sigma(x): SiLU(0) = 0, SiLU(1) = 1 / (1 + e^-1), SiLU(-x) = SiLU(x) - x."""
+    assert mlp.silu(0.0) == 0.0
+    assert abs(mlp.silu(1.0) - 1.0 / (1.0 + np.exp(-1.0))) < 1e-16
+    x = np.linspace(-5, 5, 11)
+    np.testing.assert_allclose(mlp.silu(-x), mlp.silu(x) - x, rtol=0, atol=1e-14)
+
+
+def test_forward_matches_torch_layers():
+    """The packed parameters unpacked as W [out][in] row-major and b, run through torch's own linear
+    and SiLU in FP64: a transposed weight, a swapped layer or a wrong activation would differ."""
+    torch = pytest.importorskip("torch")
+    F = torch.nn.functional
+    rng = np.random.default_rng(7)
+    theta = rng.normal(size=mlp.n_params()) * 0.2
+    X = rng.normal(size=(9, 132))
+    Y, _ = mlp.forward(theta, X)
+    t = torch.tensor(theta)
+    k, h = 0, torch.tensor(X)
+    for i, act in enumerate((True, True, False)):
+        o, n = mlp.SIZES[i + 1], mlp.SIZES[i]
+        W = t[k:k + o * n].reshape(o, n)
+        k += o * n
+        b = t[k:k + o]
+        k += o
+        h = F.linear(h, W, b)
+        if act:
+            h = F.silu(h)
+    assert k == mlp.n_params()
+    np.testing.assert_allclose(Y, h.numpy(), rtol=0, atol=1e-12)
+
+
+def test_forward_matches_scalar_loop():
+    """A one-row forward pass written as scalar loops over the packed vector (offsets counted by hand)."""
+    rng = np.random.default_rng(8)
+    theta = rng.normal(size=mlp.n_params()) * 0.2
+    x = rng.normal(size=132)
+    Y, _ = mlp.forward(theta, x[None, :])
+    h, off = list(x), 0
+    for i in range(3):
+        n_in, n_out = mlp.SIZES[i], mlp.SIZES[i + 1]
+        wofs, bofs = off, off + n_out * n_in
+        out = []
+        for r in range(n_out):
+            s = theta[bofs + r]
+            for c in range(n_in):
+                s += theta[wofs + r * n_in + c] * h[c]
+            out.append(s / (1.0 + np.exp(-s)) if i < 2 else s)
+        h, off = out, bofs + n_out
+    np.testing.assert_allclose(Y[0], h, rtol=0, atol=1e-12)
