@@ -194,9 +194,10 @@ mka_status mka_solve_columns(mka_system* sys, const int64_t* atoms, int64_t n_se
  * chunks sized to fit. The call returns MKA_ERR_INVALID_ARG, with a message,
  * when one slot and one atom's reduced problems do not fit in it; fewer slots
  * than SMs simply means fewer atoms in flight.
- * The call performs no cudaMalloc, cudaFree or other allocating routine. The
- * first call on a device looks up the array's device address (with that
- * device current) and caches it: make that first call before any stream
+ * The call performs no cudaMalloc, cudaFree or other allocating routine. Each
+ * call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress, no allocation); the first call on a device may load
+ * the library's device code there, so make that first call before any stream
  * capture. Every call on a device shares the one array, so calls whose GPU
  * work overlaps (different streams, or host threads, without ordering between
  * them) race on it and corrupt each other's results; order them on one stream.

@@ -48,7 +48,6 @@
 #include <stdint.h>
 
 #include <algorithm>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1458,30 +1457,21 @@ mka_status launch_columns(mka_system* sys, mka_result* res, const mka_solve_para
 // The same per-atom kernel, FP64 form, with its work queue counter, the atom list
 // and every per-CTA work slot carved out of one file-scope device array instead of
 // memory allocated per call. Host code cannot use the array's name as a device
-// address, so each device's address is looked up once with cudaGetSymbolAddress
-// (with that device current) and cached.
+// address: every call looks the address up with cudaGetSymbolAddress on the current
+// device (a table lookup that allocates nothing once the library's device code is
+// loaded), so that a context created anew on that device (after cudaDeviceReset, or a
+// released and re-created primary context) never sees a stale address.
 static __device__ __align__(256) unsigned char g_static_scratch[MKA_STATIC_SCRATCH_BYTES];
 
 namespace mka {
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mu;
-void* g_static_addr[kMaxDevices] = {};
-
-// Device address of g_static_scratch on the current device (looked up on first use).
+// Device address of g_static_scratch in the current device's context.
 mka_status static_scratch_address(void** out) {
-  int dev = 0;
-  MKA_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return fail(MKA_ERR_INVALID_ARG, "device index beyond the supported range");
-  std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
-    g_static_addr[dev] = p;
-  }
-  *out = g_static_addr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
+  *out = p;
   return MKA_OK;
 }
 

@@ -29,7 +29,7 @@ def lib():
 
 
 def reference_levels(mka, s, atoms, p, q):
-    res = mka.mka_solve_columns(s, atoms, mka.solve_params(p, q, cg_tol=1e-13, keep_vectors=False))
+    res = mka.mka_solve_columns(s, atoms, mka.solve_params(p, q, arith="fp64", cg_tol=1e-13, keep_vectors=False))
     try:
         return mka.mka_result_copy_levels(res)
     finally:
@@ -86,6 +86,54 @@ def test_static_scratch_in_chunks(lib):
         np.testing.assert_array_equal(got["nu_eff"], ref["nu_eff"])
         np.testing.assert_allclose(got["eps"], ref["eps"], rtol=0, atol=TOL)
         np.testing.assert_allclose(got["w"], ref["w"], rtol=0, atol=TOL)
+    finally:
+        mka.mka_system_destroy(s)
+
+
+def test_static_scratch_on_bf16_storage(lib):
+    """BF16-stored values decoded to FP64 (the allocation-free call always runs the FP64 form): the
+    same as the allocating call in FP64 arithmetic on the same stored system, twice in a row."""
+    mka = lib
+    pos, box = lattice_positions("diamond", 3.567, 3, 0.08, 0.0, 14)
+    p, q, R = 8, 8, 5.0
+    s = mka.mka_build_system(pos, box, SK_CARBON_LIKE, "bf16", cluster_radius=R)
+    try:
+        max_cl = int(mka.mka_cluster_sizes(s).max())
+        for atoms in (np.array([1, 40, 77, 180], dtype=np.int64), np.array([5, 6, 7], dtype=np.int64)):
+            ref = reference_levels(mka, s, atoms, p, q)
+            got = static_levels(mka, s, atoms, p, q, max_cl)
+            np.testing.assert_array_equal(got["status"], ref["status"])
+            np.testing.assert_array_equal(got["nu_eff"], ref["nu_eff"])
+            np.testing.assert_allclose(got["eps"], ref["eps"], rtol=0, atol=TOL)
+            np.testing.assert_allclose(got["w"], ref["w"], rtol=0, atol=TOL)
+    finally:
+        mka.mka_system_destroy(s)
+
+
+def test_static_scratch_cluster_cap(lib):
+    """max_cluster_atoms below some atoms' clusters: those atoms' columns report
+    MKA_ERR_CLUSTER_TOO_LARGE with zero levels, weights and nu_eff; the others match the
+    allocating call."""
+    mka = lib
+    pos, box = lattice_positions("fcc", 4.0, 4, 0.08, 0.08, 15)
+    from synth import SK_FCC_METAL
+    p, q, R = 6, 6, 5.5
+    s = mka.mka_build_system(pos, box, SK_FCC_METAL, "fp64", cluster_radius=R)
+    try:
+        sizes = mka.mka_cluster_sizes(s)
+        cap = int(np.median(sizes))
+        atoms = np.arange(0, pos.shape[0], 5, dtype=np.int64)
+        big = np.repeat(sizes[atoms] > cap, 4)
+        assert big.any() and (~big).any()
+        ref = reference_levels(mka, s, atoms, p, q)
+        got = static_levels(mka, s, atoms, p, q, cap)
+        assert np.all(got["status"][big] == mka.MKA_ERR_CLUSTER_TOO_LARGE)
+        assert np.all(got["nu_eff"][big] == 0)
+        assert np.all(got["eps"][big] == 0) and np.all(got["w"][big] == 0)
+        np.testing.assert_array_equal(got["status"][~big], ref["status"][~big])
+        np.testing.assert_array_equal(got["nu_eff"][~big], ref["nu_eff"][~big])
+        np.testing.assert_allclose(got["eps"][~big], ref["eps"][~big], rtol=0, atol=TOL)
+        np.testing.assert_allclose(got["w"][~big], ref["w"][~big], rtol=0, atol=TOL)
     finally:
         mka.mka_system_destroy(s)
 
