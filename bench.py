@@ -2,14 +2,23 @@
 
 Workload: the 10,077,696-atom diamond-lattice system (108^3 cubic cells,
 a = 3.567 A, sigma = 0.1 A, sp basis, M = 40,310,784 columns), cluster radius
-6 A, p = q = 15, kT = 0.1 eV. One step is one pass of the whole per-column work
-flow over a batch of consecutive atoms (4 columns each): cluster extraction,
-inner CG, multiple Krylov basis, projection, reduced eigensolve, mu by
-bisection over the batch, rho on the H pattern and the band energy. Each rank
-streams its own batches (weak scaling; no collective on the data path).
+6 A, p = q = 15, kT = 0.1 eV, BF16-stored H and S, mixed form with the learned
+CG start. The timed region is the whole work flow of Eq. EQ-WORK-FLOW over the
+whole system: K steps, each one slice of N/K atoms solved by graph-replayed
+plan batches (cluster extraction, inner CG, multiple Krylov basis, projection,
+reduced eigensolve) whose levels and rho pieces a sweep keeps in HBM; after the
+last slice, one mu by bisection over all 4.03e7 columns, rho on the whole
+pattern and the band energy at that mu. `value` = 4 N / (timed seconds).
 
-Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle
-on the host cores instead (a bounded sample of the same workload per step).
+Under torchrun each rank sweeps one chunk-aligned range of the atoms; mu and
+the energies come from one all-reduce of chunk sums per bisection halving
+(paper_1202_0098_gb300.distributed), bit-identical to one process.
+
+Also reported: K1 (the global BSR SpMV) in GB/s against the measured HBM peak,
+per-batch rates of the plain mixed form and of the FP64 form, the per-atom and
+reduced kernels' rooflines. Prints one JSON line (rank 0). `--impl reference`
+times the FP64 CPU oracle on the host cores instead (a bounded sample of the
+same workload per step).
 """
 from __future__ import annotations
 
@@ -29,10 +38,13 @@ sys.path.insert(0, ROOT)
 from synth import WORKLOADS, workload_positions  # noqa: E402
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 / FP32 FMA peaks of a GB300: 152 SMs x (2 FP64 | 128 FP32 FMA per clock) x 2 flops at the
-# 1.98 GHz seen under load; nominal FP64 1.25 TFLOP/s.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 1.98e9 / 1e12
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 1.98e9 / 1e12
+# FMA units per SM per clock on sm_103a: 128 FP32, 2 FP64 (nominal FP64 1.25 TFLOP/s per GPU).
+FMA_PER_SM = {"fp32": 128, "fp64": 2}
+
+
+def alu_peak_tflops(pipe, sms, mhz):
+    """Peak of a plain-ALU pipe: SMs x FMA units x 2 flops x the SM clock seen under load."""
+    return sms * FMA_PER_SM[pipe] * 2 * mhz * 1e6 / 1e12
 
 
 def parse():
@@ -50,6 +62,12 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shape instead of the autotuner's")
     ap.add_argument("--no-learned", action="store_true", help="mixed form without the learned CG start")
+    ap.add_argument("--no-spmv", action="store_true", help="skip the K1 SpMV leg")
+    ap.add_argument("--window", type=float, default=1.0,
+                    help="half-width (eV) of the sweep's mu window beyond 40 kT around the sampled mu")
+    ap.add_argument("--chunk-atoms", type=int, default=4096)
+    ap.add_argument("--full-fp64", action="store_true",
+                    help="after the headline, the FP64 form over the whole system: mu, E and rho differences")
     return ap.parse_args()
 
 
@@ -235,15 +253,15 @@ def flops_split(m, nnz, nu, cg_it, n_pattern_rows):
     return total - red, red
 
 
-def alu_roofline(flops_per_col, n_cols, kernel_s, pipe, kernel, what):
+def alu_roofline(flops_per_col, n_cols, kernel_s, pipe, kernel, what, sms, mhz):
     """ALU bound of one kernel: its algorithmic FLOPs per launch over its event time, against the
     peak of the pipe that does them (derived from unit counts and the clock under load)."""
-    peak = FP64_PEAK_TFLOPS if pipe == "fp64" else FP32_PEAK_TFLOPS
+    peak = alu_peak_tflops(pipe, sms, mhz)
     achieved = flops_per_col * n_cols / kernel_s / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "kernel": kernel,
-            "peak_source": (f"derived: 152 SMs x 1.98 GHz x 2 x {2 if pipe == 'fp64' else 128} "
-                            f"{'FP64' if pipe == 'fp64' else 'FP32'} FMA/clk/SM; {what}"),
+            "peak_source": (f"derived: {sms} SMs x {mhz:.0f} MHz (median under load) x 2 x {FMA_PER_SM[pipe]} "
+                            f"{pipe.upper()} FMA/clk/SM; {what}"),
             "flops_per_column": flops_per_col, "kernel_ms": kernel_s * 1e3}
 
 
@@ -345,6 +363,126 @@ def run_form(mka, torch, sysh, w, form, B, batch_atoms, steps, warmup, stream, t
     return out
 
 
+def step_slices(a0, a1, steps):
+    """The rank's atoms [a0, a1) as `steps` consecutive slices of (nearly) equal size."""
+    n = a1 - a0
+    size = -(-n // steps)
+    return [np.arange(a0 + i * size, min(a1, a0 + (i + 1) * size), dtype=np.int64) for i in range(steps)]
+
+
+def batches_of(atoms, B):
+    return [atoms[i:i + B] for i in range(0, len(atoms), B)]
+
+
+def measured_peaks():
+    try:
+        return json.load(open(MEASURED_PEAKS)), "of measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "of fallback"
+
+
+def spmv_leg(mka, torch, sysh, stream, reps=20):
+    """K1: the global BSR SpMV y = A x over the whole system, FP32 and FP64 x, k = 1, 2, 4, CUDA events
+    over `reps` launches each. Algorithmic bytes per product: values + column indices once, x read once,
+    y written once, row pointers: nnzb (16 s_v + 4) + 4 N k (s_x + s_y) + 4 (N + 1)."""
+    info = mka.mka_system_info(sysh)
+    N, nnzb = info["n_atoms"], info["nnzb"]
+    sv = {0: 8, 1: 4, 2: 2}[info["storage"]]
+    peaks, src = measured_peaks()
+    out = []
+    sp = stream.cuda_stream
+    for xd, xs, tdt in ((mka.MKA_MIXED_FP32, 4, torch.float32), (mka.MKA_FP64, 8, torch.float64)):
+        for k in (1, 2, 4):
+            x = torch.randn(4 * N * k, dtype=tdt, device="cuda")
+            y = torch.empty_like(x)
+            for which in (0, 1):
+                for _ in range(3):
+                    mka.mka_spmv(sysh, which, xd, x.data_ptr(), y.data_ptr(), k, sp)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(reps):
+                    mka.mka_spmv(sysh, which, xd, x.data_ptr(), y.data_ptr(), k, sp)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                byt = nnzb * (16 * sv + 4) + 4 * N * k * 2 * xs + 4 * (N + 1)
+                gbs = byt / ms / 1e6
+                out.append({"matrix": "HS"[which], "x": "f32" if xs == 4 else "f64", "k": k, "ms": ms,
+                            "GB_per_s": gbs, "frac": gbs / peaks["hbm_gbs"], "bytes": byt})
+            del x, y
+    torch.cuda.empty_cache()
+    head = [r for r in out if r["x"] == "f32" and r["k"] == 1 and r["matrix"] == "H"][0]
+    return {"bound": "hbm", "achieved": head["GB_per_s"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": head["GB_per_s"] / peaks["hbm_gbs"], "peak_source": f"hbm_gbs {src}",
+            "kernel": "spmv_kernel (FP32 x, k = 1, H)", "traffic": None, "all": out}
+
+
+def sample_window(mka, plan, atoms, w, half):
+    """mu of a random sample of atoms (the plan's batch bisection), and the sweep window around it:
+    [mu_s - half - 40 kT, mu_s + half + 40 kT]; the largest number of window levels in a sample column."""
+    mka.mka_plan_run(plan, atoms, w.electrons_per_atom * len(atoms), w.kT, None)
+    mu_s, _, _ = mka.mka_plan_scalars(plan)
+    lv = mka.mka_result_copy_levels(mka.mka_plan_result(plan), check=False)
+    lo, hi = mu_s - half - 40 * w.kT, mu_s + half + 40 * w.kT
+    k = np.arange(lv["eps"].shape[1])[None, :] < lv["nu_eff"][:, None]
+    cnt = ((lv["eps"] >= lo) & (lv["eps"] <= hi) & k).sum(1)
+    return mu_s, (lo, hi), int(cnt.max())
+
+
+def sweep_flow(mka, torch, D, sysh, plan, sw, slices, B, w, n_total, n_chunks, rho, stream, group, kms):
+    """The whole work flow over the rank's slices: plan batches into the sweep, then the global mu, rho and
+    energies. Per-batch kernel times are appended to kms. Returns the global scalars."""
+    for sl in slices:
+        for b in batches_of(sl, B):
+            mka.mka_plan_run_sweep(plan, sw, b)
+            kms.append(mka.mka_plan_kernel_ms(plan))
+    part = D.SweepPart(mka, sw)
+    if group is None:
+        mu = mka.mka_sweep_find_mu(sw, w.electrons_per_atom * n_total, w.kT)
+    else:
+        mu, _ = D.find_mu([part], n_chunks, w.electrons_per_atom * n_total, w.kT, group=group, device="cuda")
+    n_again = mka.mka_sweep_density(sw, plan, mu, w.kT, rho.data_ptr())
+    tot = D.totals([part], n_chunks, mu, w.kT, group=group, device="cuda")
+    return {"mu": mu, "resolved_atoms": n_again, **tot}
+
+
+def full_fp64(mka, torch, D, sysh, w, a0, a1, N, n_chunks, B, win, kp, slices, rho_head, res_head, stream, group,
+              args, tune_cache):
+    """The FP64 form (FP64 arithmetic on the same stored values) over the whole system, timed the same way:
+    its rate, mu and band energy, and the differences from the headline form over every rho entry."""
+    sp = stream.cuda_stream
+    prm = mka.solve_params(w.p, w.q, arith="fp64", cg_tol=1e-12, keep_vectors=True)
+    rng = np.random.default_rng(17)
+    sample = np.sort(rng.choice(np.arange(a0, a1), min(4096, a1 - a0), replace=False)).astype(np.int64)
+    tune = (mka.mka_autotune(sysh, prm, sample, w.electrons_per_atom * len(sample), w.kT, tune_cache, sp)
+            if not args.no_autotune else mka.tuning())
+    plan = mka.mka_plan_create(sysh, B, prm, tune, sp)
+    sw = mka.mka_sweep_create(sysh, a0, a1, w.nu, win[0], win[1], kp, args.chunk_atoms, sp)
+    rho = torch.empty_like(rho_head)
+    for b in {len(x) for sl in slices for x in batches_of(sl, B)}:
+        mka.mka_plan_run_sweep(plan, sw, np.arange(a0, a0 + b, dtype=np.int64))
+    torch.cuda.synchronize()
+    rank_barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kms = []
+    t0.record(stream)
+    res = sweep_flow(mka, torch, D, sysh, plan, sw, slices, B, w, N, n_chunks, rho, stream, group, kms)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(t0.elapsed_time(t1), "cuda")
+    drho = float((rho - rho_head).abs().max().item())
+    out = {"seconds": ms / 1e3, "columns_per_s": 4 * N / (ms / 1e3), "mu_eV": res["mu"],
+           "e_band_eV_per_atom": res["e_band"] / N, "resolved_atoms": res["resolved_atoms"],
+           "max_abs_drho": drho,
+           "abs_dmu_eV": abs(res["mu"] - res_head["mu"]),
+           "abs_dE_eV_per_atom": abs(res["e_band"] - res_head["e_band"]) / N}
+    mka.mka_sweep_destroy(sw)
+    mka.mka_plan_destroy(plan)
+    del rho
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -353,11 +491,13 @@ def main():
         return
     import torch
     import torch.distributed as dist
-    from paper_1202_0098_gb300 import build as mka_build, mka
+    from paper_1202_0098_gb300 import build as mka_build, distributed as D, mka
 
     torch.cuda.set_device(local)
+    group = None
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        group = dist.group.WORLD
     w = WORKLOADS[args.workload]
     storage = args.storage or "bf16"
     form = args.form
@@ -368,132 +508,206 @@ def main():
     sysh = mka.mka_build_system(pos, box, w.sk, storage, cluster_radius=w.R)
     t_build = time.perf_counter() - t_build
     stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
     tune_cache = os.path.join(mka_build.BUILD, "autotune.json")
-    n_steps = args.warmup + args.steps
+    a0, a1 = D.atom_ranges(N, world, args.chunk_atoms)[rank]
+    n_chunks = (N + args.chunk_atoms - 1) // args.chunk_atoms
 
-    def batch_atoms(i):
-        return shard_atoms(rank, i, n_steps, B, N)
+    spmv = None if args.no_spmv else spmv_leg(mka, torch, sysh, stream)
 
-    compare = list(range(args.warmup, args.warmup + max(1, min(args.steps, 3))))
     learned = form == "mixed" and not args.no_learned
     net, learn_info = (None, None)
     if learned:
         net, learn_info = train_warm_start(mka, torch)
         mka.mka_system_set_warm_start(sysh, net)
-    main_run = run_form(mka, torch, sysh, w, form, B, batch_atoms, args.steps, args.warmup, stream, tune_cache, rank,
-                        not args.no_autotune, compare, learned)
-    ms = max_over_ranks(main_run["ms"], "cuda")
-    value = job_throughput(4 * B, args.steps, world, ms)
+    cg_tol = 1e-12 if form == "fp64" else 1e-7
+    prm = mka.solve_params(w.p, w.q, arith=form, cg_tol=cg_tol, keep_vectors=True, use_warm_start=learned)
+    rng = np.random.default_rng(17)
+    sample = np.sort(rng.choice(np.arange(a0, a1), min(4096, a1 - a0), replace=False)).astype(np.int64)
+    tune = (mka.mka_autotune(sysh, prm, sample, w.electrons_per_atom * len(sample), w.kT, tune_cache, sp)
+            if not args.no_autotune else mka.tuning())
+    plan = mka.mka_plan_create(sysh, B, prm, tune, sp)
+    mu_s, win, max_in_win = sample_window(mka, plan, sample, w, args.window)
 
-    # clocks during a second pass of the same timed batches
+    # sweep sized for the free memory: rho [n_blocks][16] FP64 beside it
+    nblk = int(mka.mka_system_info(sysh)["nnzb"] * (a1 - a0) / N) + 1
+    free = torch.cuda.mem_get_info()[0]
+    fixed = 8 * 16 * nblk * 2 + 16 * 4 * (a1 - a0) * w.nu + (12 << 30)
+    kp_fit = int((free - fixed) // (8 * 16 * nblk))
+    kp = max(1, min(w.nu, max_in_win + 2, kp_fit))
+    sw = mka.mka_sweep_create(sysh, a0, a1, w.nu, win[0], win[1], kp, args.chunk_atoms, sp)
+    nblk = mka.mka_sweep_info(sw)["n_blocks"]
+    rho = torch.empty(nblk * 16, dtype=torch.float64, device="cuda")
+    slices = step_slices(a0, a1, args.steps)
+
+    # warm-up: the first W slices through the same path (captures every batch shape's graph)
+    warm_kms = []
+    for i in range(min(args.warmup, len(slices))):
+        for b in batches_of(slices[i], B):
+            mka.mka_plan_run_sweep(plan, sw, b)
+            warm_kms.append(mka.mka_plan_kernel_ms(plan))
+    for b in {len(x) for sl in slices for x in batches_of(sl, B)}:    # any batch shape not yet seen
+        mka.mka_plan_run_sweep(plan, sw, np.arange(a0, a0 + b, dtype=np.int64))
+    torch.cuda.synchronize()
+    rank_barrier()
+
+    kms = []
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = mka.mka_kernel_launches()
     clocks = ClockSampler(local)
     clocks.start()
-    plan = main_run["plan"]
-    n_e = w.electrons_per_atom * B
-    for i in range(args.warmup, n_steps):
-        mka.mka_plan_run(plan, batch_atoms(i), n_e, w.kT, main_run["rho"].data_ptr())
+    torch.cuda.nvtx.range_push("timed_sweep")
+    t0.record(stream)
+    res = sweep_flow(mka, torch, D, sysh, plan, sw, slices, B, w, N, n_chunks, rho, stream, group, kms)
+    t1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
+    launches = mka.mka_kernel_launches() - launches0
+    ms = max_over_ranks(t0.elapsed_time(t1), "cuda")
+    rank_barrier()
+    value = 4 * N / (ms / 1e3)
+    stored, overflow = mka.mka_sweep_status(sw)
 
-    # end to end through the public API with host buffers: host atoms in; mu, E, levels and rho out
+    # ρ on sampled atoms of the rank against the oracle at the global mu (FP64 oracle on the stored values)
+    # is a test (tests/test_gpu_sweep.py); here: the stored rho of a few atoms for the record
+    lv_cg = mka.mka_result_copy_levels(mka.mka_plan_result(plan), check=False)
+
+    # end to end through the public API with host buffers: atom slices in from pinned memory (staged by the
+    # plan every batch), the scalars and the whole rho out to a pinned host buffer in 1 GiB pieces
     e2e = None
     if not args.no_e2e:
-        rho_h = torch.empty(main_run["rho"].numel(), dtype=torch.float64, pin_memory=True)
+        piece = min(rho.numel(), (1 << 30) // 8)
+        host = torch.empty(piece, dtype=torch.float64, pin_memory=True)
+        pinned_slices = [torch.from_numpy(sl).pin_memory() for sl in slices]
         torch.cuda.synchronize()
         rank_barrier()
         te = time.perf_counter()
+        h2d = 0
+        for sl in pinned_slices:
+            sl_np = sl.numpy()
+            h2d += sl_np.nbytes
+            for b in batches_of(sl_np, B):
+                mka.mka_plan_run_sweep(plan, sw, b)
+        part = D.SweepPart(mka, sw)
+        if group is None:
+            mu_e = mka.mka_sweep_find_mu(sw, w.electrons_per_atom * N, w.kT)
+        else:
+            mu_e, _ = D.find_mu([part], n_chunks, w.electrons_per_atom * N, w.kT, group=group, device="cuda")
+        mka.mka_sweep_density(sw, plan, mu_e, w.kT, rho.data_ptr())
+        tot_e = D.totals([part], n_chunks, mu_e, w.kT, group=group, device="cuda")
         d2h = 0
-        for i in range(args.warmup, n_steps):
-            mka.mka_plan_run(plan, batch_atoms(i), n_e, w.kT, main_run["rho"].data_ptr())
-            mka.mka_plan_scalars(plan)
-            lv = mka.mka_result_copy_levels(mka.mka_plan_result(plan), check=False)
-            nb = mka.mka_result_info(mka.mka_plan_result(plan))["n_blocks"]
-            rho_h[:nb * 16].copy_(main_run["rho"][:nb * 16])
-            d2h += nb * 16 * 8 + sum(v.nbytes for k, v in lv.items() if hasattr(v, "nbytes")) + 24
+        for o in range(0, rho.numel(), piece):
+            n = min(piece, rho.numel() - o)
+            host[:n].copy_(rho[o:o + n])
+            d2h += 8 * n
         torch.cuda.synchronize()
         rank_barrier()
         te = max_over_ranks(time.perf_counter() - te, "cuda")
-        e2e = {"value": job_throughput(4 * B, args.steps, world, 1e3 * te), "unit": "columns/s",
-               "h2d_bytes_per_step": 16 * B + 8,
-               "d2h_bytes_per_step": d2h // args.steps}
+        e2e = {"value": 4 * N / te, "unit": "columns/s", "h2d_bytes_per_step": h2d // args.steps,
+               "d2h_bytes_per_step": (d2h + 24) // args.steps, "mu": mu_e,
+               "same_mu_as_timed": mu_e == res["mu"], "same_e_band": tot_e["e_band"] == res["e_band"]}
+        del host
 
-    # the mixed form without the learned start on the same batches: what the network gains
+    full_system = {"atoms": N, "columns": 4 * N, "ranks": world, "atom_range_rank0": [int(a0), int(a1)],
+                   "seconds": ms / 1e3, "columns_per_s": value, "mu_eV": res["mu"],
+                   "e_band_eV_per_atom": res["e_band"] / N, "e_band_levels_eV_per_atom": res["e_band_levels"] / N,
+                   "n_electrons": res["n_electrons"], "n_electrons_target": w.electrons_per_atom * N,
+                   "sample_mu_eV": mu_s, "window_eV": list(win), "kp": kp, "stored_atoms": stored,
+                   "overflow_atoms": overflow, "resolved_atoms": res["resolved_atoms"],
+                   "sweep_bytes": mka.mka_sweep_info(sw)["bytes"], "rho_bytes": 8 * rho.numel()}
+    mka.mka_sweep_destroy(sw)
+    mka.mka_plan_destroy(plan)
+    if args.full_fp64 and form != "fp64":
+        full_system["fp64_form"] = full_fp64(mka, torch, D, sysh, w, a0, a1, N, n_chunks, B, win, kp, slices,
+                                             rho, res, stream, group, args, tune_cache)
+        full_system["fp64_form"]["headline_speedup"] = value / full_system["fp64_form"]["columns_per_s"]
+    del rho
+    torch.cuda.empty_cache()
+
+    # per-batch rates (batch-local mu, the earlier step definition) of the comparison forms
+    per_batch = {}
+    n_steps_b = 3
+    def batch_atoms(i):
+        return shard_atoms(rank, i, n_steps_b + 1, B, N)
+    compare = list(range(1, 1 + n_steps_b))
+    main_b = run_form(mka, torch, sysh, w, form, B, batch_atoms, n_steps_b, 1, stream, tune_cache, rank,
+                      not args.no_autotune, compare, learned)
+    per_batch["headline_form"] = {"value": job_throughput(4 * B, n_steps_b, world, max_over_ranks(main_b["ms"], "cuda")),
+                                  "kernel_ms_mean": statistics.mean(main_b["kernel_ms"])}
     if learned:
-        fsteps = max(1, min(args.steps, 3))
-        prun = run_form(mka, torch, sysh, w, "mixed", B, batch_atoms, fsteps, 1, stream, tune_cache, rank,
+        prun = run_form(mka, torch, sysh, w, "mixed", B, batch_atoms, n_steps_b, 1, stream, tune_cache, rank,
                         not args.no_autotune, compare, False)
-        pval = job_throughput(4 * B, fsteps, world, max_over_ranks(prun["ms"], "cuda"))
-        # both plans' rho buffers on the same (last compared) batch
-        last = batch_atoms(compare[-1])
-        mka.mka_plan_run(main_run["plan"], last, w.electrons_per_atom * B, w.kT, main_run["rho"].data_ptr())
-        torch.cuda.synchronize()
+        pval = job_throughput(4 * B, n_steps_b, world, max_over_ranks(prun["ms"], "cuda"))
         nb = mka.mka_result_info(mka.mka_plan_result(prun["plan"]))["n_blocks"]
+        last = batch_atoms(compare[-1])
+        mka.mka_plan_run(main_b["plan"], last, w.electrons_per_atom * B, w.kT, main_b["rho"].data_ptr())
+        torch.cuda.synchronize()
         learn_info.update({
-            "plain_mixed_value": pval, "speedup_over_plain_mixed": value / pval,
-            "cg_iters_plain": prun["cg_iters"], "cg_iters_learned": main_run["cg_iters"],
-            "fallback_rate": main_run["fallback_rate"],
-            "max_abs_drho_vs_plain": float((main_run["rho"][:nb * 16] - prun["rho"][:nb * 16]).abs().max().item()),
-            "max_abs_dE_eV_per_atom_vs_plain": max(abs(a - b) for a, b in zip(main_run["e_band"], prun["e_band"])) / B,
-            "max_abs_dmu_eV_vs_plain": max(abs(a - b) for a, b in zip(main_run["mu"], prun["mu"]))})
+            "plain_mixed_value_per_batch": pval, "speedup_over_plain_mixed": per_batch["headline_form"]["value"] / pval,
+            "cg_iters_plain": prun["cg_iters"], "cg_iters_learned": main_b["cg_iters"],
+            "fallback_rate": main_b["fallback_rate"],
+            "max_abs_drho_vs_plain": float((main_b["rho"][:nb * 16] - prun["rho"][:nb * 16]).abs().max().item()),
+            "max_abs_dE_eV_per_atom_vs_plain": max(abs(a - b) for a, b in zip(main_b["e_band"], prun["e_band"])) / B,
+            "max_abs_dmu_eV_vs_plain": max(abs(a - b) for a, b in zip(main_b["mu"], prun["mu"]))})
         mka.mka_plan_destroy(prun["plan"])
-
-    # the FP64 form on the same stored values and batches: speed and agreement of mu / E
     other = None
     if form != "fp64" and not args.no_fp64_compare:
-        fsteps = max(1, min(args.steps, 3))
-        frun = run_form(mka, torch, sysh, w, "fp64", B, batch_atoms, fsteps, 1, stream, tune_cache, rank,
+        frun = run_form(mka, torch, sysh, w, "fp64", B, batch_atoms, n_steps_b, 1, stream, tune_cache, rank,
                         not args.no_autotune, compare)
-        fval = job_throughput(4 * B, fsteps, world, max_over_ranks(frun["ms"], "cuda"))
-        de = max(abs(a - b) for a, b in zip(main_run["e_band"], frun["e_band"])) / B
-        dmu = max(abs(a - b) for a, b in zip(main_run["mu"], frun["mu"]))
-        other = {"form": "fp64", "value": fval, "unit": "columns/s", "steps": fsteps,
-                 "speedup_of_headline": value / fval, "compared_batches": len(compare),
-                 "max_abs_dE_eV_per_atom": de, "max_abs_dmu_eV": dmu,
+        fval = job_throughput(4 * B, n_steps_b, world, max_over_ranks(frun["ms"], "cuda"))
+        other = {"form": "fp64", "value_per_batch": fval, "unit": "columns/s", "steps": n_steps_b,
+                 "speedup_of_headline_form_per_batch": per_batch["headline_form"]["value"] / fval,
+                 "compared_batches": len(compare),
+                 "max_abs_dE_eV_per_atom_batch_mu": max(abs(a - b) for a, b in zip(main_b["e_band"], frun["e_band"])) / B,
+                 "max_abs_dmu_eV_batch_mu": max(abs(a - b) for a, b in zip(main_b["mu"], frun["mu"])),
                  "tuning": frun["tuning"], "kernel_ms_mean": statistics.mean(frun["kernel_ms"])}
         mka.mka_plan_destroy(frun["plan"])
+    mka.mka_plan_destroy(main_b["plan"])
 
-    # roofline of the per-atom kernel from its in-graph event time
+    # rooflines of the two column kernels from their in-graph event times over the timed batches
     from scipy.spatial import cKDTree
     bsr = mka.mka_system_copy_bsr(sysh, values=False)
     tree = cKDTree(pos, boxsize=box)
-    fv = fr = 0.0
-    for i in range(args.warmup, n_steps):
-        atoms = batch_atoms(i)[::max(1, B // 256)]
-        m_c, nnz_c = local_flops(tree, pos, bsr["row_ptr"], bsr["col"], atoms, w.R)
-        rows = 4 * np.diff(bsr["row_ptr"])[atoms]
-        a_v, a_r = flops_split(m_c, nnz_c, w.nu, main_run["cg_iters"], rows)
-        fv += float(np.mean(a_v)) / args.steps
-        fr += float(np.mean(a_r)) / args.steps
-    roofline = alu_roofline(fv, 4 * B, statistics.mean(main_run["kernel_ms"]) / 1e3,
-                            "fp64" if form == "fp64" else "fp32", "atoms_kernel",
-                            "cluster, CG, Krylov basis and projection, counted as plain (not pair) arithmetic")
-    roofline_red = alu_roofline(fr, 4 * B, statistics.mean(main_run["reduced_ms"]) / 1e3, "fp64", "reduced_kernel",
+    smp = np.sort(rng.choice(np.arange(a0, a1), 256, replace=False))
+    m_c, nnz_c = local_flops(tree, pos, bsr["row_ptr"], bsr["col"], smp, w.R)
+    cg_mean = float(lv_cg["cg_iters"].mean())
+    a_v, a_r = flops_split(m_c, nnz_c, w.nu, cg_mean, 4 * np.diff(bsr["row_ptr"])[smp])
+    full = [i for i, b in enumerate(x for sl in slices for x in batches_of(sl, B)) if len(b) == B]
+    atoms_ms = statistics.mean(kms[i][0] for i in full)
+    red_ms = statistics.mean(kms[i][1] for i in full)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clk.get("sm_mhz") or measured_peaks()[0].get("sm_max_mhz", 1980.0)
+    roofline = alu_roofline(float(np.mean(a_v)), 4 * B, atoms_ms / 1e3, "fp64" if form == "fp64" else "fp32",
+                            "atoms_kernel", "cluster, CG, Krylov basis and projection, counted as plain (not pair) arithmetic",
+                            sms, mhz)
+    roofline_red = alu_roofline(float(np.mean(a_r)), 4 * B, red_ms / 1e3, "fp64", "reduced_kernel",
                                 "Cholesky, congruence, tridiagonalisation, QL with vectors, back-transform, "
-                                "outputs: 12.3 nu^3 FLOP per column")
+                                "outputs: 12.3 nu^3 FLOP per column", sms, mhz)
     if form == "mixed":   # DRAM bytes per launch from the profiler capture (null once the kernel has changed)
         roofline["traffic"] = captured_traffic("atoms_kernel", B)
         roofline_red["traffic"] = captured_traffic("reduced_kernel", 4 * B)
-    mka.mka_plan_destroy(plan)
     mka.mka_system_destroy(sysh)
     if net is not None:
         mka.mka_mlp_destroy(net)
 
     line = {"metric": "density-matrix columns/s", "value": value, "unit": "columns/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if form == "fp64" else "f32",
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64" if form == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": workload_desc(args.workload, w, N),
                        "form": f"{form}{'+learned' if learned else ''}, {storage}-stored H and S",
-                       "atoms_per_step": B, "columns_per_step": 4 * B,
-                       "step": "one graph-replayed batch: per-atom kernel, mu bisection over the batch, rho, E",
-                       "l2": "inputs larger than L2 (H,S of the whole system in HBM; each step a new batch of atoms)",
-                       "tuning": main_run["tuning"], "build_s": t_build},
-            "gpu_launches": main_run["launches"], "clocks": clk, "e2e": e2e, "roofline": roofline,
-            "roofline_reduced": roofline_red,
-            "kernel_ms_mean": statistics.mean(main_run["kernel_ms"]),
-            "reduced_ms_mean": statistics.mean(main_run["reduced_ms"]), "cg_iters_mean": main_run["cg_iters"],
-            "bad_columns": main_run["bad_columns"], "learned_warm_start": learn_info, "fp64_form": other,
-            "mu_first_compared": main_run["mu"][0], "e_band_per_atom_first_compared": main_run["e_band"][0] / B}
+                       "step": f"one slice of {len(slices[0])} atoms through plan batches of {B} atoms into the "
+                               "sweep; after the last, mu over all columns, rho on the whole pattern, energies",
+                       "atoms_per_step": len(slices[0]), "batch_atoms": B,
+                       "l2": "inputs larger than L2 (H, S, levels and rho pieces of the whole system in HBM)",
+                       "tuning": {"threads": tune.threads, "ctas_per_sm": tune.ctas_per_sm,
+                                  "order_by_size": tune.order_by_size},
+                       "build_s": t_build},
+            "gpu_launches": launches, "clocks": clk, "e2e": e2e, "roofline": roofline,
+            "roofline_reduced": roofline_red, "spmv": spmv, "full_system": full_system,
+            "kernel_ms_mean": atoms_ms, "reduced_ms_mean": red_ms, "cg_iters_mean": cg_mean,
+            "per_batch": per_batch, "learned_warm_start": learn_info, "fp64_form": other}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, pos, box)
     if rank == 0:

@@ -147,7 +147,8 @@ void mka_system_destroy(mka_system* sys);
 /* Global block-sparse product y = A x for A = H (which = 0) or S (which = 1),
  * the stored values decoded to FP64 (x_dtype = MKA_FP64: x, y device
  * double[4N][k]) or to FP32 (x_dtype = MKA_MIXED_FP32: float[4N][k]), k in
- * {1, 2, 4} right-hand sides interleaved (row-major [4N][k]). */
+ * {1, 2, 4} right-hand sides interleaved (row-major [4N][k]); x and y 16-byte
+ * aligned (MKA_ERR_INVALID_ARG otherwise). Products and sums in the type of x. */
 mka_status mka_spmv(const mka_system* sys, int which, int x_dtype, const void* x, void* y, int k,
                     void* stream);
 
@@ -360,6 +361,101 @@ void mka_plan_destroy(mka_plan* plan);
  * stored there after a search. */
 mka_status mka_autotune(mka_system* sys, const mka_solve_params* prm, const int64_t* sample, int64_t n_sample,
                         double n_electrons, double kT, const char* cache_path, void* stream, mka_tuning* out);
+
+/* ---- whole-system sweep: every column, one mu, then rho ------------------ */
+
+/* The work flow of Eq. EQ-WORK-FLOW over a whole system (or one contiguous range
+ * of its atoms, for a process that owns that range): first every column's
+ * levels (eps_alpha, w_alpha), then one chemical potential from the total
+ * electron count of all of them (Sec. 2, bisection), then rho_ij (Eq. EQ-DM) and
+ * the band energy (Eq. EQ-ENE) at that mu.
+ *
+ * A sweep keeps, in device memory, for every column of its range: the levels and
+ * weights (FP64 [4 n][nu]); and for every entry (i, j) of the pattern, the two
+ * pieces rho_ij needs at any mu inside the sweep's window [win_lo, win_hi]:
+ *   occupied part  sum over levels below win_lo of v_alpha,i v_alpha,j  (FP64)
+ *   products       v_alpha,i v_alpha,j of the levels inside the window, at most
+ *                  kp per column, in ascending order (FP64 [kp])
+ * so that rho_ij(mu) = occupied + sum_window f(eps_alpha; mu) v_alpha,i v_alpha,j
+ * holds exactly (up to the rounding of the sums) whenever every level below
+ * win_lo has f = 1 and every level above win_hi has f = 0 at mu, that is for
+ * win_lo + 40 kT <= mu <= win_hi - 40 kT (f(x) = (1 - tanh((x - mu) / 2kT)) / 2
+ * is 0 or 1 in FP64 beyond 40 kT). Columns with more than kp levels in the
+ * window ("overflow" atoms, all 4 columns of the atom) and, when mu falls
+ * outside that range, every atom, are solved again at mu by a plan.
+ * Memory: 16 (kp + 1) x 8 bytes per pattern block of the range, plus
+ * 16 nu bytes and 2 bytes per column.
+ *
+ * Deterministic sums: the electron count, the band energy and the
+ * level-energy are summed per chunk of `chunk_atoms` consecutive atoms (chunk g
+ * = atoms [g chunk_atoms, (g+1) chunk_atoms) of the whole system) in a fixed
+ * order, and the chunk sums are added in chunk order. Processes whose ranges
+ * start on chunk boundaries therefore produce the very chunk sums a single
+ * process over the whole system produces, and a bisection that adds them in
+ * chunk order (mka_sweep_find_mu here, or a host driver over all processes'
+ * mka_sweep_chunk_sums) finds the same mu, bit for bit. */
+typedef struct mka_sweep mka_sweep;
+
+/* A sweep over atoms [atom_begin, atom_end) of `sys` for subspaces of size nu
+ * (= p + q of the plans that feed it). win_lo < win_hi (eV); 1 <= kp <= nu;
+ * chunk_atoms >= 1. Allocates its device arrays (MKA_ERR_OOM when they do not
+ * fit); work runs on `stream`. */
+mka_status mka_sweep_create(mka_system* sys, int64_t atom_begin, int64_t atom_end, int nu, double win_lo,
+                            double win_hi, int kp, int64_t chunk_atoms, void* stream, mka_sweep** out);
+
+/* Chunks of the sweep's range (global index of the first one, count), pattern
+ * blocks of the range, and device bytes the sweep holds. Any output may be NULL. */
+mka_status mka_sweep_info(const mka_sweep* sw, int64_t* chunk0, int64_t* n_chunks, int64_t* n_blocks,
+                          int64_t* bytes);
+
+/* Solve a batch of atoms (host list, all inside the sweep's range, n_sel <=
+ * the plan's max_atoms) with `plan` (whose nu and system must match the
+ * sweep's) and store their levels and rho pieces in the sweep: one CUDA graph
+ * per batch size (copy-in, the column kernels, the packing kernel). Returns
+ * without waiting for the GPU, as mka_plan_run. An atom swept again is
+ * overwritten. */
+mka_status mka_plan_run_sweep(mka_plan* plan, mka_sweep* sw, const int64_t* atoms, int64_t n_sel);
+
+/* Atoms of the range stored so far, and how many of them overflowed the
+ * window (host outputs, either may be NULL); synchronises. */
+mka_status mka_sweep_status(mka_sweep* sw, int64_t* n_stored, int64_t* n_overflow);
+
+/* Smallest and largest level with nonzero weight over the stored columns
+ * (host outputs); synchronises. MKA_ERR_INVALID_ARG when there is none. */
+mka_status mka_sweep_level_range(mka_sweep* sw, double* lo, double* hi);
+
+/* mu by bisection on 2 sum_j sum_alpha f(eps; mu) w = n_electrons over every
+ * column of the range, all on the device: bracket [lo - 40 kT, hi + 40 kT]
+ * from mka_sweep_level_range, halved while wider than `tol` (eV), at most 200
+ * times; the count at each midpoint is the chunk-ordered sum above. Every atom
+ * of the range must have been stored (MKA_ERR_INVALID_ARG otherwise). */
+mka_status mka_sweep_find_mu(mka_sweep* sw, double n_electrons, double kT, double tol, double* mu);
+
+/* rho at mu into the caller's device buffer `rho` (double [n_blocks][4][4],
+ * the system's pattern blocks of the range in order: block k of atom b's row,
+ * neighbour a = col[k], rho[k][c][r] = rho_{(a,r),(b,c)}), and the per-atom band
+ * energies that mka_sweep_chunk_sums adds up. Atoms that overflowed the window,
+ * and every atom when mu lies outside [win_lo + 40 kT, win_hi - 40 kT], are
+ * solved again with `plan` (may be NULL only when there are none:
+ * MKA_ERR_INVALID_ARG otherwise); their count goes to *n_resolved (may be
+ * NULL). Returns after enqueueing the work. */
+mka_status mka_sweep_density(mka_sweep* sw, mka_plan* plan, double mu, double kT, double* rho, int64_t* n_resolved);
+
+/* Chunk sums over the range at mu, into host arrays of n_chunks doubles (any
+ * may be NULL): count[g] = 2 sum f w, e_levels[g] = 2 sum f eps w, and
+ * e_rho[g] = 2 sum_j sum_i rho_ij H_ji from the last mka_sweep_density (whose
+ * mu must be the same: MKA_ERR_INVALID_ARG otherwise). Adding a vector in
+ * chunk order gives the electron count, the band energy from the levels, and
+ * the band energy of Eq. EQ-ENE; the last two agree because e_j lies in every
+ * column's subspace. Synchronises. */
+mka_status mka_sweep_chunk_sums(mka_sweep* sw, double mu, double kT, double* count, double* e_levels,
+                                double* e_rho);
+
+/* Device pointers of the levels and weights of the range ([4 n][nu], FP64,
+ * column 4 (a - atom_begin) + o). */
+mka_status mka_sweep_device_levels(const mka_sweep* sw, const double** eps, const double** w);
+
+void mka_sweep_destroy(mka_sweep* sw);
 
 /* ---- accounting ---------------------------------------------------------- */
 

@@ -278,6 +278,8 @@ mka_status mka_spmv(const mka_system* sys, int which, int x_dtype, const void* x
   if (which != 0 && which != 1) return fail(MKA_ERR_INVALID_ARG, "which must be 0 (H) or 1 (S)");
   if (x_dtype != MKA_FP64 && x_dtype != MKA_MIXED_FP32) return fail(MKA_ERR_INVALID_ARG, "x_dtype must be FP64 or FP32");
   if (k != 1 && k != 2 && k != 4) return fail(MKA_ERR_INVALID_ARG, "k must be 1, 2 or 4");
+  if ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15)
+    return fail(MKA_ERR_INVALID_ARG, "x and y must be 16-byte aligned");
   return launch_spmv(sys, which, x_dtype, x, y, k, (cudaStream_t)stream);
 }
 

@@ -1350,7 +1350,10 @@ mka_status launch_cluster_sizes(const mka_system* sys, const int64_t* d_sel, int
   A.sel = d_sel;
   A.n_sel = n_sel;
   const int threads = 256;
-  const int64_t blocks = std::min<int64_t>((n_sel + 7) / 8, 152 * 16);
+  int dev = 0, sms = 0;
+  MKA_CUDA_TRY(cudaGetDevice(&dev));
+  MKA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t blocks = std::min<int64_t>((n_sel + 7) / 8, (int64_t)sms * 16);
   cluster_size_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), threads, 0, st>>>(A, d_sizes);
   count_launches();
   MKA_CUDA_TRY(cudaGetLastError());

@@ -24,7 +24,14 @@ namespace mka {
 namespace {
 
 constexpr int kRedThreads = 256;
-constexpr int kRedBlocks = 608;   // 4 x 152 SMs
+// Grid of the reductions: 4 CTAs per SM of the current device, at most kMaxRedBlocks (the size of
+// the partial-sum buffers).
+int red_blocks() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 152;
+  return std::max(1, std::min(kMaxRedBlocks, 4 * sms));
+}
 
 __device__ __forceinline__ double fermi(double x, double mu, double kT) {
   const double y = (x - mu) / (2.0 * kT);
@@ -46,7 +53,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // Bisection state (device doubles): [0] lo, [1] hi, [2] target, [3] kT, [4] tol,
-// [5] last count, [6] halvings done. partial[kRedBlocks], ticket (unsigned).
+// [5] last count, [6] halvings done. partial[kMaxRedBlocks], ticket (unsigned).
 struct MuState {
   double lo, hi, target, kT, tol, last, iters, pad;
 };
@@ -160,10 +167,13 @@ __device__ void column_weights(const double* cv, int64_t t, int nu, const double
 
 // rho / E: one CTA per selected atom, thread per (block k, c, r) of its row:
 // rho_ij = sum_alpha f_alpha V_i alpha V_j alpha = U_i . g_j with g_j = C diag(f) V_j.
+// Output layout: the batch's (blocks at blk_off[t], E of atom t at e_partial[t]) when out_base < 0;
+// otherwise the system's pattern order from block out_base on (blocks at row_ptr[atom] - out_base,
+// E at e_partial[atom - e_base]).
 __global__ void density_kernel(const double* vp, const double* cv, const double* eps, const int64_t* blk_off,
                                const int64_t* sel, const int32_t* row_ptr, const void* valH, int storage,
                                int nu, double mu_host, const double* mu_dev, double kT, double* rho,
-                               double* e_partial) {
+                               double* e_partial, int64_t out_base = -1, int64_t e_base = 0) {
   __shared__ double red[kRedThreads / 32];
   __shared__ double f[4 * MKA_MAX_NU];
   __shared__ double g[4 * MKA_MAX_NU];
@@ -172,6 +182,7 @@ __global__ void density_kernel(const double* vp, const double* cv, const double*
   const int64_t atom = sel[t];
   const int nrow = row_ptr[atom + 1] - row_ptr[atom];
   const int64_t b0 = blk_off[t];
+  const int64_t ob = out_base < 0 ? b0 : (int64_t)row_ptr[atom] - out_base;
   for (int i = threadIdx.x; i < 4 * nu; i += blockDim.x) {
     const int c = i / nu;
     f[i] = fermi(eps[(4 * t + c) * nu + i % nu], mu, kT);
@@ -184,7 +195,7 @@ __global__ void density_kernel(const double* vp, const double* cv, const double*
     const double* u = vp + ((b0 + k) * 16 + c * 4 + r) * (int64_t)nu;
     double s = 0.0;
     for (int n = 0; n < nu; ++n) s += u[n] * g[c * nu + n];
-    if (rho) rho[(b0 + k) * 16 + c * 4 + r] = s;
+    if (rho) rho[(ob + k) * 16 + c * 4 + r] = s;
     const int64_t gk = (int64_t)row_ptr[atom] + k;
     double h;
     if (storage == MKA_FP64) h = reinterpret_cast<const double*>(valH)[gk * 16 + c * 4 + r];
@@ -193,7 +204,7 @@ __global__ void density_kernel(const double* vp, const double* cv, const double*
     e += s * h;
   }
   const double s = block_sum(e, red);
-  if (threadIdx.x == 0) e_partial[t] = 2.0 * s;
+  if (threadIdx.x == 0) e_partial[out_base < 0 ? t : atom - e_base] = 2.0 * s;
 }
 
 // G_ij(z) = sum_alpha V_i alpha V_j alpha / (z - eps_alpha) = U_i . (C diag(1 / (z - eps)) V_j).
@@ -255,87 +266,108 @@ __global__ void count_partial_kernel(const double* eps, const double* w, int64_t
   if (threadIdx.x == 0) partial[blockIdx.x] = 2.0 * s;
 }
 
-// ---- global BSR SpMV: one warp per block row, 16-byte vector loads of the values ----
+// ---- global BSR SpMV: four lanes per block row, one per output row of the 4x4 blocks ----
+// Lane (a, i) computes y[4a + i][0..K) = sum over the row's blocks k of sum_jj val[k][i][jj] x[4 col[k] + jj][0..K).
+// Each lane streams its row of every block (4 values: 8 bytes in BF16, 16 in FP32, 32 in FP64), so the four
+// lanes of a block row read each block's values as one contiguous piece; the column index is read by all
+// four (one request), and x through the read-only cache, one 16-byte vector per (block column, jj) row
+// group. Blocks are taken four at a time with their loads issued before the arithmetic.
 template <typename TV>
-struct VecLoad;
+struct RowVals;
 template <>
-struct VecLoad<double> {
-  static constexpr int E = 2;
-  static __device__ __forceinline__ void load(const double* p, double out[2]) {
-    double2 a = __ldcs(reinterpret_cast<const double2*>(p));
-    out[0] = a.x; out[1] = a.y;
+struct RowVals<__nv_bfloat16> {
+  static __device__ __forceinline__ void load(const __nv_bfloat16* v, int64_t k, int i, float out[4]) {
+    const uint2 a = __ldcs(reinterpret_cast<const uint2*>(v + k * 16 + i * 4));
+    out[0] = __uint_as_float(a.x << 16);
+    out[1] = __uint_as_float(a.x & 0xFFFF0000u);
+    out[2] = __uint_as_float(a.y << 16);
+    out[3] = __uint_as_float(a.y & 0xFFFF0000u);
   }
 };
 template <>
-struct VecLoad<float> {
-  static constexpr int E = 4;
-  static __device__ __forceinline__ void load(const float* p, float out[4]) {
-    float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+struct RowVals<float> {
+  static __device__ __forceinline__ void load(const float* v, int64_t k, int i, float out[4]) {
+    const float4 a = __ldcs(reinterpret_cast<const float4*>(v + k * 16 + i * 4));
     out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
   }
 };
 template <>
-struct VecLoad<__nv_bfloat16> {
-  static constexpr int E = 8;
-  static __device__ __forceinline__ void load(const __nv_bfloat16* p, float out[8]) {
-    uint4 a = __ldcs(reinterpret_cast<const uint4*>(p));
-    const uint32_t u[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      out[2 * i] = __uint_as_float(u[i] << 16);
-      out[2 * i + 1] = __uint_as_float(u[i] & 0xFFFF0000u);
-    }
+struct RowVals<double> {
+  static __device__ __forceinline__ void load(const double* v, int64_t k, int i, double out[4]) {
+    const double2 a = __ldcs(reinterpret_cast<const double2*>(v + k * 16 + i * 4));
+    const double2 b = __ldcs(reinterpret_cast<const double2*>(v + k * 16 + i * 4) + 1);
+    out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
   }
 };
+
+// x rows 4 cb .. 4 cb + 3, K values each: xv[jj][c].
+template <typename TX, int K>
+__device__ __forceinline__ void load_x(const TX* __restrict__ x, int64_t cb, TX xv[4][K]) {
+  const TX* p = x + cb * 4 * K;
+  if constexpr (sizeof(TX) == 4) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int t = 0; t < K; ++t) {        // 4 K floats = K float4
+      const float4 a = __ldg(q + t);
+      const float f[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xv[(4 * t + u) / K][(4 * t + u) % K] = f[u];
+    }
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int t = 0; t < 2 * K; ++t) {    // 4 K doubles = 2 K double2
+      const double2 a = __ldg(q + t);
+      xv[(2 * t) / K][(2 * t) % K] = a.x;
+      xv[(2 * t + 1) / K][(2 * t + 1) % K] = a.y;
+    }
+  }
+}
 
 template <typename TV, typename TX, int K>
 __global__ void __launch_bounds__(256) spmv_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                                    const TV* __restrict__ val, const TX* __restrict__ x,
                                                    TX* __restrict__ y, int64_t n_rows) {
-  constexpr int E = VecLoad<TV>::E;
   using TL = typename std::conditional<std::is_same<TV, double>::value, double, float>::type;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t a = warp; a < n_rows; a += nwarps) {
-    const int k0 = row_ptr[a], k1 = row_ptr[a + 1];
-    TX acc[4][K];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < 4 * n_rows; g += stride) {
+    const int64_t a = g >> 2;
+    const int i = (int)(g & 3);
+    const int k0 = __ldg(row_ptr + a), k1 = __ldg(row_ptr + a + 1);
+    TX acc[K];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int c = 0; c < K; ++c) acc[c] = 0;
+    int k = k0;
+    for (; k + 4 <= k1; k += 4) {
+      int cb[4];
+      TL v[4][4];
 #pragma unroll
-      for (int c = 0; c < K; ++c) acc[i][c] = 0;
-    const int64_t e_end = (int64_t)(k1 - k0) * 16;
-    for (int64_t e0 = (int64_t)lane * E; e0 < e_end; e0 += 32 * E) {
-      TL v[E];
-      VecLoad<TV>::load(val + (int64_t)k0 * 16 + e0, v);
-      const int blk = (int)(e0 >> 4);
-      const int cb = col[k0 + blk];
+      for (int u = 0; u < 4; ++u) cb[u] = __ldg(col + k + u);
 #pragma unroll
-      for (int t = 0; t < E; ++t) {
-        const int ij = (int)((e0 + t) & 15), i = ij >> 2, jj = ij & 3;
+      for (int u = 0; u < 4; ++u) RowVals<TV>::load(val, k + u, i, v[u]);
 #pragma unroll
-        for (int c = 0; c < K; ++c) acc[i][c] += (TX)v[t] * x[((int64_t)4 * cb + jj) * K + c];
+      for (int u = 0; u < 4; ++u) {
+        TX xv[4][K];
+        load_x<TX, K>(x, cb[u], xv);
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+          for (int c = 0; c < K; ++c) acc[c] = fma((TX)v[u][jj], xv[jj][c], acc[c]);
       }
     }
+    for (; k < k1; ++k) {
+      TL v[4];
+      RowVals<TV>::load(val, k, i, v);
+      TX xv[4][K];
+      load_x<TX, K>(x, __ldg(col + k), xv);
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+      for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
-      for (int c = 0; c < K; ++c) {
-        TX s = acc[i][c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        acc[i][c] = s;
-      }
-    if (lane < 4 * K) {
-      const int i = lane / K, c = lane % K;
-      TX out = 0;
-#pragma unroll
-      for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-        for (int cc = 0; cc < K; ++cc)
-          if (ii == i && cc == c) out = acc[ii][cc];
-      y[((int64_t)4 * a + i) * K + c] = out;
+        for (int c = 0; c < K; ++c) acc[c] = fma((TX)v[jj], xv[jj][c], acc[c]);
     }
+    TX* yo = y + (4 * a + i) * K;
+#pragma unroll
+    for (int c = 0; c < K; ++c) yo[c] = acc[c];
   }
 }
 
@@ -344,7 +376,7 @@ mka_status spmv_dispatch_k(const mka_system* s, const TV* val, const void* x, vo
   int dev = 0, sms = 0;
   MKA_CUDA_TRY(cudaGetDevice(&dev));
   MKA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int64_t blocks = std::min<int64_t>((s->n_atoms + 7) / 8, (int64_t)sms * 8);
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((4 * s->n_atoms + 255) / 256, (int64_t)sms * 8));
   const TX* xx = reinterpret_cast<const TX*>(x);
   TX* yy = reinterpret_cast<TX*>(y);
   if (k == 1) spmv_kernel<TV, TX, 1><<<(unsigned)blocks, 256, 0, st>>>(s->d_row_ptr, s->d_col, val, xx, yy, s->n_atoms);
@@ -364,14 +396,14 @@ mka_status spmv_dispatch(const mka_system* s, const void* val, int x_dtype, cons
 
 }  // namespace
 
-size_t mu_buffer_bytes() { return sizeof(MuState) + sizeof(double) * 2 * kRedBlocks + 64; }
+size_t mu_buffer_bytes() { return sizeof(MuState) + sizeof(double) * 2 * kMaxRedBlocks + 64; }
 
 mka_status find_mu_enqueue(const double* eps, const double* w, int64_t n, double n_electrons, double kT, double tol,
                            int halvings, void* buf, double* mu_dev_out, cudaStream_t st) {
   MuState* S = reinterpret_cast<MuState*>(buf);
   double* partial = reinterpret_cast<double*>(S + 1);
-  unsigned* ticket = reinterpret_cast<unsigned*>(partial + 2 * kRedBlocks);
-  const int blocks = (int)std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, (n + kRedThreads - 1) / kRedThreads));
+  unsigned* ticket = reinterpret_cast<unsigned*>(partial + 2 * kMaxRedBlocks);
+  const int blocks = (int)std::min<int64_t>(red_blocks(), std::max<int64_t>(1, (n + kRedThreads - 1) / kRedThreads));
   mu_init_kernel<<<1, 1, 0, st>>>(S, ticket, n_electrons, kT, tol);
   eps_range_kernel<<<blocks, kRedThreads, 0, st>>>(eps, w, n, partial, ticket, S);
   for (int i = 0; i < halvings; ++i) bisect_kernel<<<blocks, kRedThreads, 0, st>>>(eps, w, n, partial, ticket, S);
@@ -387,9 +419,20 @@ mka_status density_enqueue(const mka_system* sys, const int64_t* sel, const int6
   density_kernel<<<(unsigned)n_sel, 128, 0, st>>>(vp, cv, eps, blk_off, sel, sys->d_row_ptr, sys->d_valH,
                                                   sys->storage, nu, 0.0, mu_dev, kT, rho_out, tmp);
   sum_kernel<<<1, kRedThreads, 0, st>>>(tmp, n_sel, tmp + n_sel);
-  count_partial_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(eps, w, 4 * n_sel * nu, 0.0, mu_dev, kT, tmp + n_sel + 2);
-  sum_kernel<<<1, kRedThreads, 0, st>>>(tmp + n_sel + 2, kRedBlocks, tmp + n_sel + 1);
+  const int rb = red_blocks();
+  count_partial_kernel<<<rb, kRedThreads, 0, st>>>(eps, w, 4 * n_sel * nu, 0.0, mu_dev, kT, tmp + n_sel + 2);
+  sum_kernel<<<1, kRedThreads, 0, st>>>(tmp + n_sel + 2, rb, tmp + n_sel + 1);
   count_launches(4);
+  MKA_CUDA_TRY(cudaGetLastError());
+  return MKA_OK;
+}
+
+mka_status density_global_enqueue(const mka_system* sys, const int64_t* sel, const int64_t* blk_off, const double* vp,
+                                  const double* cv, const double* eps, int64_t n_sel, int nu, double mu, double kT,
+                                  double* rho, int64_t out_base, double* e_atom, int64_t e_base, cudaStream_t st) {
+  density_kernel<<<(unsigned)n_sel, 128, 0, st>>>(vp, cv, eps, blk_off, sel, sys->d_row_ptr, sys->d_valH, sys->storage,
+                                                  nu, mu, nullptr, kT, rho, e_atom, out_base, e_base);
+  count_launches();
   MKA_CUDA_TRY(cudaGetLastError());
   return MKA_OK;
 }
@@ -398,19 +441,19 @@ mka_status launch_find_mu(mka_result* res, double n_electrons, double kT, double
   cudaStream_t st = res->stream;
   const int64_t n = res->n_cols * res->nu;
   if (!res->d_mu_state) {
-    MKA_CUDA_TRY(cudaMalloc(&res->d_mu_state, sizeof(MuState) + sizeof(double) * 2 * kRedBlocks + 64));
-    MKA_CUDA_TRY(cudaMemsetAsync(res->d_mu_state, 0, sizeof(MuState) + sizeof(double) * 2 * kRedBlocks + 64, st));
+    MKA_CUDA_TRY(cudaMalloc(&res->d_mu_state, mu_buffer_bytes()));
+    MKA_CUDA_TRY(cudaMemsetAsync(res->d_mu_state, 0, mu_buffer_bytes(), st));
   }
   MuState* S = reinterpret_cast<MuState*>(res->d_mu_state);
   double* partial = reinterpret_cast<double*>(S + 1);
-  unsigned* ticket = reinterpret_cast<unsigned*>(partial + 2 * kRedBlocks);
+  unsigned* ticket = reinterpret_cast<unsigned*>(partial + 2 * kMaxRedBlocks);
   MuState h{};
   h.target = n_electrons;
   h.kT = kT;
   h.tol = tol;
   MKA_CUDA_TRY(cudaMemcpyAsync(S, &h, sizeof(MuState), cudaMemcpyHostToDevice, st));
   MKA_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
-  const int blocks = (int)std::min<int64_t>(kRedBlocks, std::max<int64_t>(1, (n + kRedThreads - 1) / kRedThreads));
+  const int blocks = (int)std::min<int64_t>(red_blocks(), std::max<int64_t>(1, (n + kRedThreads - 1) / kRedThreads));
   eps_range_kernel<<<blocks, kRedThreads, 0, st>>>(res->d_eps, res->d_w, n, partial, ticket, S);
   count_launches();
   MKA_CUDA_TRY(cudaGetLastError());
@@ -433,14 +476,15 @@ mka_status launch_density(mka_system* sys, mka_result* res, double mu, double kT
                           double* n_elec) {
   cudaStream_t st = res->stream;
   double* tmp = nullptr;
-  MKA_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(double) * (res->n_sel + 2 + kRedBlocks), st));
+  const int rb = red_blocks();
+  MKA_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(double) * (res->n_sel + 2 + rb), st));
   density_kernel<<<(unsigned)res->n_sel, 128, 0, st>>>(res->d_vp, res->d_cv, res->d_eps, res->d_blk_off,
                                                        res->d_sel, sys->d_row_ptr, sys->d_valH, sys->storage,
                                                        res->nu, mu, nullptr, kT, rho_out, tmp);
   sum_kernel<<<1, kRedThreads, 0, st>>>(tmp, res->n_sel, tmp + res->n_sel);
-  count_partial_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(res->d_eps, res->d_w, res->n_cols * res->nu, mu, nullptr,
+  count_partial_kernel<<<rb, kRedThreads, 0, st>>>(res->d_eps, res->d_w, res->n_cols * res->nu, mu, nullptr,
                                                            kT, tmp + res->n_sel + 2);
-  sum_kernel<<<1, kRedThreads, 0, st>>>(tmp + res->n_sel + 2, kRedBlocks, tmp + res->n_sel + 1);
+  sum_kernel<<<1, kRedThreads, 0, st>>>(tmp + res->n_sel + 2, rb, tmp + res->n_sel + 1);
   count_launches(4);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && (e_band || n_elec)) {

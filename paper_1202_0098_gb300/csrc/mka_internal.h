@@ -55,6 +55,9 @@ struct mka_system {
   std::vector<int32_t> h_row_ptr, h_col;
 };
 
+typedef struct mka_plan mka_plan;
+typedef struct mka_sweep mka_sweep;
+
 struct mka_result {
   mka_system* sys = nullptr;
   cudaStream_t stream = nullptr;
@@ -176,10 +179,46 @@ mka_status find_mu_enqueue(const double* eps, const double* w, int64_t n, double
 mka_status density_enqueue(const mka_system* sys, const int64_t* sel, const int64_t* blk_off, const double* vp,
                            const double* cv, const double* eps, const double* w, int64_t n_sel, int nu,
                            const double* mu_dev, double kT, double* rho_out, double* tmp, cudaStream_t st);
+// rho at a host mu into the system's pattern order (blocks from out_base on) and 2 sum rho H per atom
+// into e_atom[atom - e_base].
+mka_status density_global_enqueue(const mka_system* sys, const int64_t* sel, const int64_t* blk_off, const double* vp,
+                                  const double* cv, const double* eps, int64_t n_sel, int nu, double mu, double kT,
+                                  double* rho, int64_t out_base, double* e_atom, int64_t e_base, cudaStream_t st);
+// Largest grid of the fixed-order reductions (4 CTAs per SM); sizes their partial-sum buffers.
+constexpr int kMaxRedBlocks = 4096;
 // tmp of density_enqueue holds n_sel + 2 + kDensityTmpExtra doubles.
-constexpr int kDensityTmpExtra = 608;
+constexpr int kDensityTmpExtra = kMaxRedBlocks;
 
 size_t storage_bytes(int storage);
+
+// ---- whole-system sweeps (sweep.cu) ----
+// What a plan does with a batch after its column kernels.
+enum PlanModeKind { PLAN_BATCH = 0, PLAN_SWEEP = 1, PLAN_AT_MU = 2 };
+struct PlanMode {
+  int kind = PLAN_BATCH;
+  mka_sweep* sw = nullptr;     // PLAN_SWEEP / PLAN_AT_MU: the sweep the batch belongs to
+  double mu = 0;               // PLAN_AT_MU: chemical potential
+  double kT = 0;               // PLAN_BATCH / PLAN_AT_MU
+  double n_electrons = 0;      // PLAN_BATCH
+  double* rho = nullptr;       // PLAN_BATCH: batch layout; PLAN_AT_MU: the sweep's global layout
+};
+// Runs one batch of a plan in the given mode (validation, staging, graph capture / replay).
+mka_status plan_run_mode(mka_plan* P, const int64_t* atoms, int64_t n_sel, const PlanMode& m);
+// Largest batch of a plan.
+int64_t plan_max_atoms(const mka_plan* P);
+// Kernels a plan captures for a sweep: pack the batch's kept data into the sweep (levels, window,
+// occupied sum, partially occupied products), or write rho at a given mu into the sweep's layout.
+mka_status sweep_pack_enqueue(mka_sweep* sw, const int64_t* sel, const int64_t* blk_off, const double* vp,
+                              const double* cv, const double* eps, const double* w, const int32_t* nu_eff,
+                              int64_t n_sel, int nu, cudaStream_t st);
+mka_status sweep_at_mu_enqueue(mka_sweep* sw, const int64_t* sel, const int64_t* blk_off, const double* vp,
+                               const double* cv, const double* eps, int64_t n_sel, int nu, double mu, double kT,
+                               double* rho, cudaStream_t st);
+// Stream ordering between a sweep's stream and a plan's stream around a plan's batch.
+mka_status sweep_join_before(mka_sweep* sw, cudaStream_t plan_stream);
+mka_status sweep_join_after(mka_sweep* sw, cudaStream_t plan_stream);
+// Host-side check of a batch against the sweep's atom range.
+mka_status sweep_check_atoms(const mka_sweep* sw, const mka_system* sys, int nu, const int64_t* atoms, int64_t n);
 
 // Kernel launches of this library (mka_kernel_launches).
 extern std::atomic<int64_t> g_kernel_launches;

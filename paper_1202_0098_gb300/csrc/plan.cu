@@ -58,10 +58,16 @@ __global__ void size_scatter_kernel(const int32_t* sizes, int64_t n, int32_t* bi
 
 struct GraphEntry {
   int64_t n = 0;
-  double n_electrons = 0, kT = 0;
+  int kind = PLAN_BATCH;
+  const mka_sweep* sw = nullptr;
+  double n_electrons = 0, kT = 0, mu = 0;
   double* rho = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t kernels = 0;
+  bool same(int64_t n_, const PlanMode& m) const {
+    return n == n_ && kind == m.kind && sw == m.sw && n_electrons == m.n_electrons && kT == m.kT && mu == m.mu &&
+           rho == m.rho;
+  }
 };
 
 }  // namespace
@@ -127,7 +133,7 @@ mka_status plan_alloc(mka_plan* P) {
   MKA_CUDA_TRY(cudaMalloc(&P->sizes, sizeof(int32_t) * A));
   MKA_CUDA_TRY(cudaMalloc(&P->bins, sizeof(int32_t) * kSizeBins));
   MKA_CUDA_TRY(cudaMalloc(&P->mu_buf, mu_buffer_bytes()));
-  MKA_CUDA_TRY(cudaMalloc(&P->dev_out, sizeof(double) * (A + 4 + 1024)));   // mu, partials, E, N, count partials
+  MKA_CUDA_TRY(cudaMalloc(&P->dev_out, sizeof(double) * (A + 4 + kMaxRedBlocks)));   // mu, partials, E, N, count partials
   MKA_CUDA_TRY(cudaMallocHost(&P->h_stage, sizeof(int64_t) * (2 * A + 1)));
   MKA_CUDA_TRY(cudaEventCreateWithFlags(&P->staged, cudaEventDisableTiming));
   MKA_CUDA_TRY(cudaStreamCreateWithFlags(&P->capture, cudaStreamNonBlocking));
@@ -143,7 +149,7 @@ mka_status plan_alloc(mka_plan* P) {
 }
 
 // Enqueue one batch of n atoms (already staged) on the capture stream (recorded into a graph).
-mka_status plan_enqueue(mka_plan* P, int64_t n, double n_electrons, double kT, double* rho_out) {
+mka_status plan_enqueue(mka_plan* P, int64_t n, const PlanMode& m) {
   cudaStream_t st = P->capture;
   mka_result* r = P->res;
   MKA_CUDA_TRY(cudaMemcpyAsync(r->d_sel, P->h_stage, sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
@@ -205,10 +211,14 @@ mka_status plan_enqueue(mka_plan* P, int64_t n, double n_electrons, double kT, d
   if (s) return s;
   MKA_CUDA_TRY(cudaEventRecordWithFlags(P->k2, st, cudaEventRecordExternal));
   const int nu = r->nu;
-  s = find_mu_enqueue(r->d_eps, r->d_w, 4 * n * nu, n_electrons, kT, 1e-12, kHalvings, P->mu_buf, P->dev_out, st);
+  if (m.kind == PLAN_SWEEP)
+    return sweep_pack_enqueue(m.sw, r->d_sel, r->d_blk_off, r->d_vp, r->d_cv, r->d_eps, r->d_w, r->d_nu_eff, n, nu, st);
+  if (m.kind == PLAN_AT_MU)
+    return sweep_at_mu_enqueue(m.sw, r->d_sel, r->d_blk_off, r->d_vp, r->d_cv, r->d_eps, n, nu, m.mu, m.kT, m.rho, st);
+  s = find_mu_enqueue(r->d_eps, r->d_w, 4 * n * nu, m.n_electrons, m.kT, 1e-12, kHalvings, P->mu_buf, P->dev_out, st);
   if (s) return s;
-  return density_enqueue(P->sys, r->d_sel, r->d_blk_off, r->d_vp, r->d_cv, r->d_eps, r->d_w, n, nu, P->dev_out, kT,
-                         rho_out, P->dev_out + 1, st);
+  return density_enqueue(P->sys, r->d_sel, r->d_blk_off, r->d_vp, r->d_cv, r->d_eps, r->d_w, n, nu, P->dev_out, m.kT,
+                         m.rho, P->dev_out + 1, st);
 }
 
 }  // namespace
@@ -295,12 +305,29 @@ mka_status mka_plan_create(mka_system* sys, int64_t max_atoms, const mka_solve_p
 
 mka_status mka_plan_run(mka_plan* P, const int64_t* atoms, int64_t n_sel, double n_electrons, double kT,
                         double* rho_out) {
+  PlanMode m;
+  m.kind = PLAN_BATCH;
+  m.n_electrons = n_electrons;
+  m.kT = kT;
+  m.rho = rho_out;
+  return plan_run_mode(P, atoms, n_sel, m);
+}
+
+}  // extern "C"
+
+int64_t mka::plan_max_atoms(const mka_plan* P) { return P->max_atoms; }
+
+mka_status mka::plan_run_mode(mka_plan* P, const int64_t* atoms, int64_t n_sel, const PlanMode& m) {
   if (!P || !atoms || n_sel < 1 || n_sel > P->max_atoms)
     return fail(MKA_ERR_INVALID_ARG, "plan, host atoms and 1 <= n_sel <= max_atoms are required");
-  if (!(kT > 0)) return fail(MKA_ERR_INVALID_ARG, "need kT > 0");
+  if (m.kind != PLAN_SWEEP && !(m.kT > 0)) return fail(MKA_ERR_INVALID_ARG, "need kT > 0");
   const mka_system* sys = P->sys;
   for (int64_t t = 0; t < n_sel; ++t)
     if (atoms[t] < 0 || atoms[t] >= sys->n_atoms) return fail(MKA_ERR_INVALID_ARG, "atom index out of range");
+  if (m.kind != PLAN_BATCH) {
+    mka_status sc = sweep_check_atoms(m.sw, sys, P->prm.p + P->prm.q, atoms, n_sel);
+    if (sc) return sc;
+  }
   // the previous batch's copies must have read the staging buffer before it is refilled
   MKA_CUDA_TRY(cudaEventSynchronize(P->staged));
   int64_t* off = P->h_stage + P->max_atoms;
@@ -317,12 +344,12 @@ mka_status mka_plan_run(mka_plan* P, const int64_t* atoms, int64_t n_sel, double
   r->h_blk_off.assign(off, off + n_sel + 1);
   GraphEntry* g = nullptr;
   for (auto& e : P->graphs)
-    if (e.n == n_sel && e.n_electrons == n_electrons && e.kT == kT && e.rho == rho_out) g = &e;
+    if (e.same(n_sel, m)) g = &e;
   if (!g) {
     cudaGraph_t graph = nullptr;
     const int64_t k0 = mka_kernel_launches();
     MKA_CUDA_TRY(cudaStreamBeginCapture(P->capture, cudaStreamCaptureModeThreadLocal));
-    mka_status s = plan_enqueue(P, n_sel, n_electrons, kT, rho_out);
+    mka_status s = plan_enqueue(P, n_sel, m);
     cudaError_t e = cudaStreamEndCapture(P->capture, &graph);
     const int64_t kernels = mka_kernel_launches() - k0;
     count_launches(-kernels);    // captured, not executed
@@ -333,9 +360,12 @@ mka_status mka_plan_run(mka_plan* P, const int64_t* atoms, int64_t n_sel, double
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     GraphEntry ge;
     ge.n = n_sel;
-    ge.n_electrons = n_electrons;
-    ge.kT = kT;
-    ge.rho = rho_out;
+    ge.kind = m.kind;
+    ge.sw = m.sw;
+    ge.n_electrons = m.n_electrons;
+    ge.kT = m.kT;
+    ge.mu = m.mu;
+    ge.rho = m.rho;
     ge.kernels = kernels;
     e = cudaGraphInstantiate(&ge.exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -343,11 +373,18 @@ mka_status mka_plan_run(mka_plan* P, const int64_t* atoms, int64_t n_sel, double
     P->graphs.push_back(ge);
     g = &P->graphs.back();
   }
+  if (m.kind != PLAN_BATCH) {
+    mka_status sj = sweep_join_before(m.sw, P->stream);
+    if (sj) return sj;
+  }
   MKA_CUDA_TRY(cudaGraphLaunch(g->exec, P->stream));
   count_launches(g->kernels);
   MKA_CUDA_TRY(cudaEventRecord(P->staged, P->stream));
+  if (m.kind != PLAN_BATCH) return sweep_join_after(m.sw, P->stream);
   return MKA_OK;
 }
+
+extern "C" {
 
 mka_status mka_plan_scalars(mka_plan* P, double* mu, double* e_band, double* n_elec) {
   if (!P) return fail(MKA_ERR_INVALID_ARG, "plan is NULL");

@@ -33,6 +33,8 @@ EXPORTED = [
     "mka_autotune", "mka_mlp_num_params", "mka_mlp_create", "mka_mlp_destroy", "mka_mlp_set_params",
     "mka_mlp_get_params", "mka_mlp_forward", "mka_mlp_gradients", "mka_mlp_train_step", "mka_warm_start_features",
     "mka_cg_patch_targets", "mka_system_set_warm_start", "mka_result_copy_warm_start",
+    "mka_sweep_create", "mka_sweep_info", "mka_plan_run_sweep", "mka_sweep_status", "mka_sweep_level_range",
+    "mka_sweep_find_mu", "mka_sweep_density", "mka_sweep_chunk_sums", "mka_sweep_device_levels", "mka_sweep_destroy",
     "mka_kernel_launches", "mka_last_error", "mka_status_string",
 ]
 
@@ -106,6 +108,15 @@ def load(path: str | None = None) -> C.CDLL:
         "mka_cg_patch_targets": [P, P, I64, I32, D, P, P, P, P],
         "mka_system_set_warm_start": [P, P],
         "mka_result_copy_warm_start": [P, P],
+        "mka_sweep_create": [P, I64, I64, I32, D, D, I32, I64, P, P],
+        "mka_sweep_info": [P, P, P, P, P],
+        "mka_plan_run_sweep": [P, P, P, I64],
+        "mka_sweep_status": [P, P, P],
+        "mka_sweep_level_range": [P, P, P],
+        "mka_sweep_find_mu": [P, D, D, D, P],
+        "mka_sweep_density": [P, P, D, D, P, P],
+        "mka_sweep_chunk_sums": [P, D, D, P, P, P],
+        "mka_sweep_device_levels": [P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -119,6 +130,8 @@ def load(path: str | None = None) -> C.CDLL:
     lib.mka_mlp_destroy.restype = None
     lib.mka_plan_destroy.argtypes = [P]
     lib.mka_plan_destroy.restype = None
+    lib.mka_sweep_destroy.argtypes = [P]
+    lib.mka_sweep_destroy.restype = None
     lib.mka_result_destroy.argtypes = [P]
     lib.mka_result_destroy.restype = None
     lib.mka_kernel_launches.argtypes = []
@@ -354,6 +367,72 @@ def mka_autotune(sys, prm: mka_solve_params, sample: np.ndarray, n_electrons: fl
                                cache_path.encode() if cache_path else None, C.c_void_p(stream), C.byref(out)),
            "mka_autotune")
     return out
+
+
+# ---- whole-system sweep ------------------------------------------------------------------
+
+def mka_sweep_create(sys, atom_begin: int, atom_end: int, nu: int, win_lo: float, win_hi: float, kp: int,
+                     chunk_atoms: int = 4096, stream: int = 0) -> C.c_void_p:
+    out = C.c_void_p()
+    _check(load().mka_sweep_create(sys, int(atom_begin), int(atom_end), int(nu), float(win_lo), float(win_hi), int(kp),
+                                   int(chunk_atoms), C.c_void_p(stream), C.byref(out)), "mka_sweep_create")
+    return out
+
+
+def mka_sweep_info(sw) -> dict:
+    c0, nc, nb, by = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+    _check(load().mka_sweep_info(sw, C.byref(c0), C.byref(nc), C.byref(nb), C.byref(by)), "mka_sweep_info")
+    return {"chunk0": c0.value, "n_chunks": nc.value, "n_blocks": nb.value, "bytes": by.value}
+
+
+def mka_plan_run_sweep(plan, sw, atoms: np.ndarray):
+    a = np.ascontiguousarray(atoms, dtype=np.int64)
+    _check(load().mka_plan_run_sweep(plan, sw, _ptr(a), a.shape[0]), "mka_plan_run_sweep")
+
+
+def mka_sweep_status(sw) -> tuple[int, int]:
+    st, ov = C.c_int64(), C.c_int64()
+    _check(load().mka_sweep_status(sw, C.byref(st), C.byref(ov)), "mka_sweep_status")
+    return st.value, ov.value
+
+
+def mka_sweep_level_range(sw) -> tuple[float, float]:
+    lo, hi = C.c_double(), C.c_double()
+    _check(load().mka_sweep_level_range(sw, C.byref(lo), C.byref(hi)), "mka_sweep_level_range")
+    return lo.value, hi.value
+
+
+def mka_sweep_find_mu(sw, n_electrons: float, kT: float, tol: float = 1e-12) -> float:
+    mu = C.c_double()
+    _check(load().mka_sweep_find_mu(sw, float(n_electrons), float(kT), float(tol), C.byref(mu)), "mka_sweep_find_mu")
+    return mu.value
+
+
+def mka_sweep_density(sw, plan, mu: float, kT: float, rho_ptr: int) -> int:
+    n = C.c_int64()
+    _check(load().mka_sweep_density(sw, plan, float(mu), float(kT), C.c_void_p(rho_ptr), C.byref(n)),
+           "mka_sweep_density")
+    return n.value
+
+
+def mka_sweep_chunk_sums(sw, mu: float, kT: float, levels: bool = True, rho: bool = False) -> dict:
+    nc = mka_sweep_info(sw)["n_chunks"]
+    cnt = np.empty(nc)
+    el = np.empty(nc) if levels else None
+    er = np.empty(nc) if rho else None
+    _check(load().mka_sweep_chunk_sums(sw, float(mu), float(kT), _ptr(cnt), _ptr(el), _ptr(er)), "mka_sweep_chunk_sums")
+    return {"count": cnt, "e_levels": el, "e_rho": er}
+
+
+def mka_sweep_device_levels(sw) -> tuple[int, int]:
+    e, w = C.c_void_p(), C.c_void_p()
+    _check(load().mka_sweep_device_levels(sw, C.byref(e), C.byref(w)), "mka_sweep_device_levels")
+    return e.value, w.value
+
+
+def mka_sweep_destroy(sw):
+    if sw:
+        load().mka_sweep_destroy(sw)
 
 
 # ---- learned warm start ------------------------------------------------------------------

@@ -67,7 +67,10 @@ def test_forward_gradient_and_adam_match_oracle(lib):
         Lo, go = omlp.loss_and_grad(theta_b, X.astype(np.float64), T.astype(np.float64))
         assert abs(loss.item() - Lo) <= 1e-4 * Lo
         gg = g.cpu().numpy()
-        assert np.linalg.norm(gg - go) <= 1e-3 * np.linalg.norm(go)
+        # element by element: FP32 sums of FP32 activations against FP64 (parameters BF16-rounded on both
+        # sides); the floor 1e-5 max|g| covers entries that are sums cancelling to near zero
+        np.testing.assert_allclose(gg, go, rtol=1e-3, atol=1e-5 * np.abs(go).max())
+        assert np.linalg.norm(gg - go) <= 1e-4 * np.linalg.norm(go)
         theta = mka.mka_mlp_get_params(net).astype(np.float64)
         mka.mka_mlp_train_step(net, Xd.data_ptr(), Td.data_ptr(), B, 1e-3)
         ref, _, _ = omlp.adam_step(theta, gg.astype(np.float64), np.zeros_like(theta), np.zeros_like(theta), 1)
