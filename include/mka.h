@@ -251,6 +251,16 @@ mka_status mka_density_energy(mka_system* sys, mka_result* res, double mu, doubl
  * [n_blocks][4][4][2]. Needs keep_vectors = 1. */
 mka_status mka_greens(mka_system* sys, mka_result* res, double z_re, double z_im, double* g_out);
 
+/* Energy density matrix pi_ij = sum_alpha f(eps_alpha; mu) eps_alpha v_alpha,i v_alpha,j
+ * (Sec. 2, after Eq. EQ-DM) on the selected rows' pattern, layout as rho in
+ * mka_density_energy (device double [n_blocks][4][4], may be NULL), and the
+ * forces of Eqs. EQ-FORCE / EQ-FORCE-PART from the result's columns, ADDED to
+ * the caller's device double [n_atoms][3] (may be NULL): F_K += -2 sum_j sum_i
+ * (rho_ij dH_ji/dR_K - pi_ij dS_ji/dR_K) (sign as for mka_sweep_forces). The adds
+ * are atomic, so the last bits may differ between runs. Needs keep_vectors = 1
+ * and a system built by mka_build_system (MKA_ERR_INVALID_ARG otherwise). */
+mka_status mka_forces(mka_system* sys, mka_result* res, double mu, double kT, double* pi_out, double* forces);
+
 /* ---- learned warm start for the inner CG ---------------------------------- */
 /* The inner CG for s_j = S^{-1} e_j (Sec. 2) may start from any x0. A small
  * network predicts x0 on the 17-atom patch around j's atom (the atom and its 16
@@ -398,10 +408,13 @@ typedef struct mka_sweep mka_sweep;
 
 /* A sweep over atoms [atom_begin, atom_end) of `sys` for subspaces of size nu
  * (= p + q of the plans that feed it). win_lo < win_hi (eV); 1 <= kp <= nu;
- * chunk_atoms >= 1. Allocates its device arrays (MKA_ERR_OOM when they do not
- * fit); work runs on `stream`. */
+ * chunk_atoms >= 1. with_forces = 1 also keeps the occupied part of the energy
+ * density matrix pi (16 more doubles per pattern block) and 3 doubles per block
+ * for mka_sweep_forces (needs a system built by mka_build_system). Allocates
+ * its device arrays (MKA_ERR_OOM when they do not fit); work runs on `stream`. */
 mka_status mka_sweep_create(mka_system* sys, int64_t atom_begin, int64_t atom_end, int nu, double win_lo,
-                            double win_hi, int kp, int64_t chunk_atoms, void* stream, mka_sweep** out);
+                            double win_hi, int kp, int64_t chunk_atoms, int with_forces, void* stream,
+                            mka_sweep** out);
 
 /* Chunks of the sweep's range (global index of the first one, count), pattern
  * blocks of the range, and device bytes the sweep holds. Any output may be NULL. */
@@ -440,6 +453,21 @@ mka_status mka_sweep_find_mu(mka_sweep* sw, double n_electrons, double kT, doubl
  * MKA_ERR_INVALID_ARG otherwise); their count goes to *n_resolved (may be
  * NULL). Returns after enqueueing the work. */
 mka_status mka_sweep_density(mka_sweep* sw, mka_plan* plan, double mu, double kT, double* rho, int64_t* n_resolved);
+
+/* Forces on every atom of the system from the sweep's columns (Eqs. EQ-FORCE,
+ * EQ-FORCE-PART) at mu: F_K = -2 sum_j sum_i (rho_ij dH_ji/dR_K - pi_ij dS_ji/dR_K)
+ * over the range's columns j and their pattern entries i, with pi_ij =
+ * sum_alpha f eps_alpha v_alpha,i v_alpha,j the energy density matrix (Sec. 2)
+ * and the Slater-Koster block derivatives of the model at the current
+ * positions. The sign of the pi term is that of the derivative of the grand
+ * potential at fixed mu (dOmega = 2 (Tr[rho dH] - Tr[pi dS])). Output: device
+ * double [n_atoms][3] (eV/A), overwritten; atoms outside the range get the
+ * contributions of the range's columns only (a process's share, to be summed
+ * over processes). The sums run in a fixed order. Overflowed atoms (or all,
+ * when mu is outside the window's range, as for mka_sweep_density) are solved
+ * again with `plan`; their count goes to *n_resolved (may be NULL). Needs a
+ * sweep created with with_forces = 1. */
+mka_status mka_sweep_forces(mka_sweep* sw, mka_plan* plan, double mu, double kT, double* forces, int64_t* n_resolved);
 
 /* Chunk sums over the range at mu, into host arrays of n_chunks doubles (any
  * may be NULL): count[g] = 2 sum f w, e_levels[g] = 2 sum f eps w, and

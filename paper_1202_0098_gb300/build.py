@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmka.so")
-SOURCES = ["system.cpp", "api.cpp", "columns.cu", "reduced.cu", "global.cu", "plan.cu", "mlp.cu", "sweep.cu"]
+SOURCES = ["system.cpp", "api.cpp", "columns.cu", "reduced.cu", "global.cu", "plan.cu", "mlp.cu", "sweep.cu", "forces.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-fopenmp,-ffp-contract=off",
           "-I" + os.path.join(os.path.dirname(HERE), "include")]

@@ -49,6 +49,8 @@ struct mka_system {
   double* d_pos = nullptr;      // [n_atoms][3], wrapped into the box
   float* d_posf = nullptr;      // the same rounded to FP32 (distance prefilter)
   mka_mlp* warm = nullptr;      // network used when a solve asks for the learned warm start (not owned)
+  mka_sk_params sk{};           // the model's Slater-Koster parameters (forces need their derivatives)
+  bool have_sk = false;         // false for a caller's BSR matrices: no forces
   int max_cluster = -1;         // largest cluster over all atoms (-1: not computed yet)
   mka::CellList cells{};
   // host copies of the pattern
@@ -201,6 +203,7 @@ struct PlanMode {
   double kT = 0;               // PLAN_BATCH / PLAN_AT_MU
   double n_electrons = 0;      // PLAN_BATCH
   double* rho = nullptr;       // PLAN_BATCH: batch layout; PLAN_AT_MU: the sweep's global layout
+  bool forces = false;         // PLAN_AT_MU: force contributions of the batch's blocks instead of rho
 };
 // Runs one batch of a plan in the given mode (validation, staging, graph capture / replay).
 mka_status plan_run_mode(mka_plan* P, const int64_t* atoms, int64_t n_sel, const PlanMode& m);
@@ -213,7 +216,15 @@ mka_status sweep_pack_enqueue(mka_sweep* sw, const int64_t* sel, const int64_t* 
                               int64_t n_sel, int nu, cudaStream_t st);
 mka_status sweep_at_mu_enqueue(mka_sweep* sw, const int64_t* sel, const int64_t* blk_off, const double* vp,
                                const double* cv, const double* eps, int64_t n_sel, int nu, double mu, double kT,
-                               double* rho, cudaStream_t st);
+                               double* rho, bool forces, cudaStream_t st);
+// Forces (forces.cu): per-block contributions g = -2 sum_{c,r} (rho dH/dd - pi dS/dd) of the selected atoms'
+// blocks (batch layout when out_base < 0, else the system's blocks from out_base on), pi on the pattern
+// (may be NULL); and F_K from the blocks of atoms [a0, a1) for every atom of the system.
+mka_status force_blocks_enqueue(const mka_system* sys, const int64_t* sel, const int64_t* blk_off, const double* vp,
+                                const double* cv, const double* eps, int64_t n_sel, int nu, double mu, double kT,
+                                int64_t out_base, double* pi, double* g, cudaStream_t st);
+mka_status force_gather_enqueue(const mka_system* sys, const double* g, int64_t a0, int64_t a1, int64_t blk0, double* F,
+                                cudaStream_t st);
 // Stream ordering between a sweep's stream and a plan's stream around a plan's batch.
 mka_status sweep_join_before(mka_sweep* sw, cudaStream_t plan_stream);
 mka_status sweep_join_after(mka_sweep* sw, cudaStream_t plan_stream);

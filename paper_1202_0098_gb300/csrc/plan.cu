@@ -64,9 +64,10 @@ struct GraphEntry {
   double* rho = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t kernels = 0;
+  bool forces = false;
   bool same(int64_t n_, const PlanMode& m) const {
     return n == n_ && kind == m.kind && sw == m.sw && n_electrons == m.n_electrons && kT == m.kT && mu == m.mu &&
-           rho == m.rho;
+           rho == m.rho && forces == m.forces;
   }
 };
 
@@ -214,7 +215,8 @@ mka_status plan_enqueue(mka_plan* P, int64_t n, const PlanMode& m) {
   if (m.kind == PLAN_SWEEP)
     return sweep_pack_enqueue(m.sw, r->d_sel, r->d_blk_off, r->d_vp, r->d_cv, r->d_eps, r->d_w, r->d_nu_eff, n, nu, st);
   if (m.kind == PLAN_AT_MU)
-    return sweep_at_mu_enqueue(m.sw, r->d_sel, r->d_blk_off, r->d_vp, r->d_cv, r->d_eps, n, nu, m.mu, m.kT, m.rho, st);
+    return sweep_at_mu_enqueue(m.sw, r->d_sel, r->d_blk_off, r->d_vp, r->d_cv, r->d_eps, n, nu, m.mu, m.kT, m.rho,
+                               m.forces, st);
   s = find_mu_enqueue(r->d_eps, r->d_w, 4 * n * nu, m.n_electrons, m.kT, 1e-12, kHalvings, P->mu_buf, P->dev_out, st);
   if (s) return s;
   return density_enqueue(P->sys, r->d_sel, r->d_blk_off, r->d_vp, r->d_cv, r->d_eps, r->d_w, n, nu, P->dev_out, m.kT,
@@ -366,6 +368,7 @@ mka_status mka::plan_run_mode(mka_plan* P, const int64_t* atoms, int64_t n_sel, 
     ge.kT = m.kT;
     ge.mu = m.mu;
     ge.rho = m.rho;
+    ge.forces = m.forces;
     ge.kernels = kernels;
     e = cudaGraphInstantiate(&ge.exec, graph, 0);
     cudaGraphDestroy(graph);

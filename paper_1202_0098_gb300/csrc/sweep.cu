@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "mka_internal.h"
+#include "sk_grad.cuh"
 
 namespace mka {
 namespace {
@@ -83,6 +84,7 @@ struct PackArgs {
   uint8_t* g_flag;
   double* g_occ;
   double* g_part;
+  double* g_occ_pi;          // occupied part of pi (NULL: not kept)
 };
 
 // One CTA per atom of the batch. Shared memory: g_below [4][nu] = C diag(1_below) V_j and
@@ -124,14 +126,21 @@ __global__ void __launch_bounds__(128) sweep_pack_kernel(const PackArgs A) {
   }
   double* gb = sm;
   double* W = sm + 4 * nu;
+  double* gbp = W + (size_t)4 * nu * kp;     // pi's occupied part: C diag(eps 1_below) V_j
   for (int i = threadIdx.x; i < 4 * nu; i += blockDim.x) {
     const int c = i / nu, n = i % nu;
     const int64_t col = 4 * t + c;
     const double* b = A.cv + (size_t)(col >> 5) * kept_block_doubles(nu) * 32 + (col & 31);
     const int lo = s_lo[c], cnt = s_cnt[c];
-    double g = 0.0;
-    for (int a = 0; a < lo; ++a) g += b[(size_t)(n * nu + a) * 32] * b[(size_t)(nu * nu + a) * 32];
+    const double* ec = A.eps + (4 * t + c) * nu;
+    double g = 0.0, gp = 0.0;
+    for (int a = 0; a < lo; ++a) {
+      const double cv = b[(size_t)(n * nu + a) * 32] * b[(size_t)(nu * nu + a) * 32];
+      g += cv;
+      gp += cv * ec[a];
+    }
     gb[i] = g;
+    if (A.g_occ_pi) gbp[i] = gp;
     for (int a = 0; a < kp; ++a)
       W[(size_t)(c * nu + n) * kp + a] =
           a < cnt ? b[(size_t)(n * nu + lo + a) * 32] * b[(size_t)(nu * nu + lo + a) * 32] : 0.0;
@@ -153,6 +162,12 @@ __global__ void __launch_bounds__(128) sweep_pack_kernel(const PackArgs A) {
     for (int n = 0; n < nu; ++n) occ += u[n] * g[n];
     const int64_t e = (gk0 + k) * 16 + c * 4 + r;
     A.g_occ[e] = occ;
+    if (A.g_occ_pi) {
+      const double* gp = gbp + c * nu;
+      double op = 0.0;
+      for (int n = 0; n < nu; ++n) op += u[n] * gp[n];
+      A.g_occ_pi[e] = op;
+    }
     double* out = A.g_part + e * kp;
     for (int a = 0; a < kp; ++a) {
       double s = 0.0;
@@ -326,7 +341,84 @@ __global__ void __launch_bounds__(256) sweep_rho_kernel(const RhoArgs A) {
   }
 }
 
-size_t pack_smem_bytes(int nu, int kp) { return sizeof(double) * 4 * (size_t)nu * (kp + 1); }
+// Forces from the stored pieces: one warp per atom, lanes 0-15 on one block's 16 entries and 16-31 on the
+// next; rho and pi at mu, the entries' contributions -2 (rho dH/dd - pi dS/dd) summed per block by a fixed
+// xor tree into g[block] (3 doubles).
+struct ForceArgs {
+  const double* eps;
+  const uint8_t* win;
+  const uint8_t* flag;
+  const double* occ;
+  const double* occ_pi;
+  const double* part;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const double* pos;
+  double box[3];
+  double Vh[4], Vs[4], d0;
+  int nu, kp;
+  int64_t a0, n, blk0;
+  double mu, kT;
+  double* g;
+};
+
+__global__ void __launch_bounds__(256) sweep_force_kernel(const ForceArgs A) {
+  extern __shared__ double fsm[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int kp = A.kp, nu = A.nu;
+  double* f = fsm + (size_t)wid * 8 * kp;         // [4][kp] occupations, then [4][kp] f eps
+  double* fe = f + 4 * kp;
+  for (int64_t la = (int64_t)blockIdx.x * nw + wid; la < A.n; la += (int64_t)gridDim.x * nw) {
+    if (A.flag[la] != 1) continue;
+    for (int i = lane; i < 4 * kp; i += 32) {
+      const int c = i / kp, a = i % kp;
+      const uint8_t* wn = A.win + 2 * (4 * la + c);
+      const double x = a < wn[1] ? A.eps[(4 * la + c) * nu + wn[0] + a] : 0.0;
+      const double fx = a < wn[1] ? fermi_f(x, A.mu, A.kT) : 0.0;
+      f[i] = fx;
+      fe[i] = fx * x;
+    }
+    __syncwarp();
+    const int64_t atom = A.a0 + la;
+    const int64_t k0 = A.row_ptr[atom];
+    const int nrow = A.row_ptr[atom + 1] - (int)k0;
+    const int64_t gk0 = k0 - A.blk0;
+    const double ax = A.pos[3 * atom], ay = A.pos[3 * atom + 1], az = A.pos[3 * atom + 2];
+    for (int base = 0; base < nrow * 16; base += 32) {
+      const int i = base + lane;
+      const bool on = i < nrow * 16;
+      const int k = i >> 4, c = (i >> 2) & 3, r = i & 3;
+      double e[3] = {0.0, 0.0, 0.0};
+      if (on) {
+        const int64_t idx = (gk0 + k) * 16 + (i & 15);
+        double rho = A.occ[idx], pi = A.occ_pi[idx];
+        const double* p = A.part + idx * kp;
+        for (int a = 0; a < kp; ++a) {
+          rho += f[c * kp + a] * p[a];
+          pi += fe[c * kp + a] * p[a];
+        }
+        const int64_t b = A.col[k0 + k];
+        if (b != atom) {
+          double d[3] = {A.pos[3 * b] - ax, A.pos[3 * b + 1] - ay, A.pos[3 * b + 2] - az};
+          for (int q = 0; q < 3; ++q) d[q] -= A.box[q] * rint(d[q] / A.box[q]);
+          double gh[3], gs[3];
+          sk_entry_grad(d, A.Vh, A.d0, c, r, gh);
+          sk_entry_grad(d, A.Vs, A.d0, c, r, gs);
+          for (int q = 0; q < 3; ++q) e[q] = -2.0 * (rho * gh[q] - pi * gs[q]);
+        }
+      }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) e[q] += __shfl_xor_sync(0xffffffffu, e[q], o);
+      if (on && (lane & 15) == 0)
+        for (int q = 0; q < 3; ++q) A.g[(gk0 + k) * 3 + q] = e[q];
+    }
+    __syncwarp();
+  }
+}
+
+size_t pack_smem_bytes(int nu, int kp) { return sizeof(double) * 4 * (size_t)nu * (kp + 2); }
 
 }  // namespace
 }  // namespace mka
@@ -346,6 +438,8 @@ struct mka_sweep {
   double* d_occ = nullptr;              // [nblk][16]
   double* d_part = nullptr;             // [nblk][16][kp]
   double* d_eatom = nullptr;            // [n] 2 sum rho H of the atom's columns (after a density)
+  double* d_occ_pi = nullptr;           // [nblk][16] occupied part of pi (sweeps made for forces)
+  double* d_g = nullptr;                // [nblk][3] force contribution of each block
   double* d_chunk = nullptr;            // [3][n_chunks]
   double* d_range = nullptr;            // [2 kRangeBlocks]
   mka::BisState* d_state = nullptr;
@@ -391,6 +485,7 @@ mka_status sweep_pack_enqueue(mka_sweep* sw, const int64_t* sel, const int64_t* 
   A.g_flag = sw->d_flag;
   A.g_occ = sw->d_occ;
   A.g_part = sw->d_part;
+  A.g_occ_pi = sw->d_occ_pi;
   sweep_pack_kernel<<<(unsigned)n_sel, 128, pack_smem_bytes(nu, sw->kp), st>>>(A);
   count_launches();
   MKA_CUDA_TRY(cudaGetLastError());
@@ -399,7 +494,9 @@ mka_status sweep_pack_enqueue(mka_sweep* sw, const int64_t* sel, const int64_t* 
 
 mka_status sweep_at_mu_enqueue(mka_sweep* sw, const int64_t* sel, const int64_t* blk_off, const double* vp,
                                const double* cv, const double* eps, int64_t n_sel, int nu, double mu, double kT,
-                               double* rho, cudaStream_t st) {
+                               double* rho, bool forces, cudaStream_t st) {
+  if (forces)
+    return force_blocks_enqueue(sw->sys, sel, blk_off, vp, cv, eps, n_sel, nu, mu, kT, sw->blk0, nullptr, sw->d_g, st);
   return density_global_enqueue(sw->sys, sel, blk_off, vp, cv, eps, n_sel, nu, mu, kT, rho, sw->blk0, sw->d_eatom,
                                 sw->a0, st);
 }
@@ -466,6 +563,8 @@ void mka_sweep_destroy(mka_sweep* sw) {
   cudaFree(sw->d_occ);
   cudaFree(sw->d_part);
   cudaFree(sw->d_eatom);
+  cudaFree(sw->d_occ_pi);
+  cudaFree(sw->d_g);
   cudaFree(sw->d_chunk);
   cudaFree(sw->d_range);
   cudaFree(sw->d_state);
@@ -475,7 +574,7 @@ void mka_sweep_destroy(mka_sweep* sw) {
 }
 
 mka_status mka_sweep_create(mka_system* sys, int64_t atom_begin, int64_t atom_end, int nu, double win_lo,
-                            double win_hi, int kp, int64_t chunk_atoms, void* stream, mka_sweep** out) {
+                            double win_hi, int kp, int64_t chunk_atoms, int with_forces, void* stream, mka_sweep** out) {
   if (!out) return fail(MKA_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!sys) return fail(MKA_ERR_INVALID_ARG, "system is NULL");
@@ -485,6 +584,7 @@ mka_status mka_sweep_create(mka_system* sys, int64_t atom_begin, int64_t atom_en
   if (kp < 1 || kp > nu) return fail(MKA_ERR_INVALID_ARG, "need 1 <= kp <= nu");
   if (!(win_lo < win_hi)) return fail(MKA_ERR_INVALID_ARG, "need win_lo < win_hi");
   if (chunk_atoms < 1) return fail(MKA_ERR_INVALID_ARG, "need chunk_atoms >= 1");
+  if (with_forces && !sys->have_sk) return fail(MKA_ERR_INVALID_ARG, "forces need the Slater-Koster model (mka_build_system)");
   mka_sweep* sw = new mka_sweep();
   sw->sys = sys;
   sw->stream = (cudaStream_t)stream;
@@ -515,6 +615,10 @@ mka_status mka_sweep_create(mka_system* sys, int64_t atom_begin, int64_t atom_en
   ALLOC(sw->d_occ, sizeof(double) * 16 * sw->nblk);
   ALLOC(sw->d_part, sizeof(double) * 16 * sw->nblk * kp);
   ALLOC(sw->d_eatom, sizeof(double) * n);
+  if (with_forces) {
+    ALLOC(sw->d_occ_pi, sizeof(double) * 16 * sw->nblk);
+    ALLOC(sw->d_g, sizeof(double) * 3 * sw->nblk);
+  }
   ALLOC(sw->d_chunk, sizeof(double) * 3 * sw->n_chunks);
   ALLOC(sw->d_range, sizeof(double) * 2 * kRangeBlocks);
   ALLOC(sw->d_state, sizeof(BisState));
@@ -529,6 +633,9 @@ mka_status mka_sweep_create(mka_system* sys, int64_t atom_begin, int64_t atom_en
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(sweep_rho_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(double) * 8 * 4 * kp));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sweep_force_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * 8 * 8 * kp));
   if (e != cudaSuccess) {
     const bool oom = e == cudaErrorMemoryAllocation;
     cudaGetLastError();
@@ -684,6 +791,84 @@ mka_status mka_sweep_density(mka_sweep* sw, mka_plan* plan, double mu, double kT
   }
   sw->rho_mu = mu;
   sw->rho_kT = kT;
+  if (n_resolved) *n_resolved = n_again;
+  return MKA_OK;
+}
+
+mka_status mka_sweep_forces(mka_sweep* sw, mka_plan* plan, double mu, double kT, double* forces, int64_t* n_resolved) {
+  if (!sw || !forces) return fail(MKA_ERR_INVALID_ARG, "sweep and forces are required");
+  if (!sw->d_g) return fail(MKA_ERR_INVALID_ARG, "the sweep was created without forces");
+  if (!(kT > 0)) return fail(MKA_ERR_INVALID_ARG, "need kT > 0");
+  int64_t stored = 0, overflow = 0;
+  mka_status s = flag_counts(sw, &stored, &overflow);
+  if (s) return s;
+  if (stored != sw->n)
+    return fail(MKA_ERR_INVALID_ARG, std::to_string(sw->n - stored) + " atoms of the sweep's range are not stored yet");
+  const bool inside = sw->win_lo + 40.0 * kT <= mu && mu <= sw->win_hi - 40.0 * kT;
+  cudaStream_t st = sw->stream;
+  const mka_system* sys = sw->sys;
+  if (inside) {
+    ForceArgs A{};
+    A.eps = sw->d_eps;
+    A.win = sw->d_win;
+    A.flag = sw->d_flag;
+    A.occ = sw->d_occ;
+    A.occ_pi = sw->d_occ_pi;
+    A.part = sw->d_part;
+    A.row_ptr = sys->d_row_ptr;
+    A.col = sys->d_col;
+    A.pos = sys->d_pos;
+    for (int q = 0; q < 3; ++q) A.box[q] = sys->box[q];
+    for (int q = 0; q < 4; ++q) {
+      A.Vh[q] = sys->sk.V[q];
+      A.Vs[q] = sys->sk.Sv[q];
+    }
+    A.d0 = sys->sk.d0;
+    A.nu = sw->nu;
+    A.kp = sw->kp;
+    A.a0 = sw->a0;
+    A.n = sw->n;
+    A.blk0 = sw->blk0;
+    A.mu = mu;
+    A.kT = kT;
+    A.g = sw->d_g;
+    int dev = 0, sms = 0;
+    MKA_CUDA_TRY(cudaGetDevice(&dev));
+    MKA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t blocks = std::min<int64_t>((sw->n + 7) / 8, (int64_t)sms * 8);
+    sweep_force_kernel<<<(unsigned)std::max<int64_t>(1, blocks), 256, sizeof(double) * 8 * 8 * sw->kp, st>>>(A);
+    count_launches();
+    MKA_CUDA_TRY(cudaGetLastError());
+  }
+  const int64_t n_again = inside ? overflow : sw->n;
+  if (n_again > 0) {
+    if (!plan) return fail(MKA_ERR_INVALID_ARG, std::to_string(n_again) + " atoms must be solved again at mu; pass a plan");
+    std::vector<int64_t> again;
+    again.reserve(n_again);
+    if (inside) {
+      std::vector<uint8_t> fl(sw->n);
+      MKA_CUDA_TRY(cudaMemcpyAsync(fl.data(), sw->d_flag, sw->n, cudaMemcpyDeviceToHost, st));
+      MKA_CUDA_TRY(cudaStreamSynchronize(st));
+      for (int64_t i = 0; i < sw->n; ++i)
+        if (fl[i] & 2) again.push_back(sw->a0 + i);
+    } else {
+      for (int64_t i = 0; i < sw->n; ++i) again.push_back(sw->a0 + i);
+    }
+    const int64_t B = plan_max_atoms(plan);
+    PlanMode m;
+    m.kind = PLAN_AT_MU;
+    m.sw = sw;
+    m.mu = mu;
+    m.kT = kT;
+    m.forces = true;
+    for (size_t off = 0; off < again.size(); off += (size_t)B) {
+      const int64_t cnt = std::min<int64_t>(B, (int64_t)again.size() - (int64_t)off);
+      s = plan_run_mode(plan, again.data() + off, cnt, m);
+      if (s) return s;
+    }
+  }
+  s = force_gather_enqueue(sys, sw->d_g, sw->a0, sw->a1, sw->blk0, forces, st);
+  if (s) return s;
   if (n_resolved) *n_resolved = n_again;
   return MKA_OK;
 }

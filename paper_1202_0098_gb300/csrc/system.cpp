@@ -273,6 +273,8 @@ mka_status mka_build_system(const double* pos, int64_t n_atoms, const double box
   s->storage = storage;
   s->R = cluster_radius;
   s->stream = (cudaStream_t)stream;
+  s->sk = *sk;
+  s->have_sk = true;
   for (int d = 0; d < 3; ++d) s->box[d] = box[d];
   std::vector<double> wpos = wrap_positions(pos, n_atoms, box);
   HostCells hc = make_cells(wpos, n_atoms, box, sk->rc);

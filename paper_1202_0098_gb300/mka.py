@@ -34,7 +34,8 @@ EXPORTED = [
     "mka_mlp_get_params", "mka_mlp_forward", "mka_mlp_gradients", "mka_mlp_train_step", "mka_warm_start_features",
     "mka_cg_patch_targets", "mka_system_set_warm_start", "mka_result_copy_warm_start",
     "mka_sweep_create", "mka_sweep_info", "mka_plan_run_sweep", "mka_sweep_status", "mka_sweep_level_range",
-    "mka_sweep_find_mu", "mka_sweep_density", "mka_sweep_chunk_sums", "mka_sweep_device_levels", "mka_sweep_destroy",
+    "mka_sweep_find_mu", "mka_sweep_density", "mka_sweep_forces", "mka_sweep_chunk_sums", "mka_sweep_device_levels",
+    "mka_sweep_destroy", "mka_forces",
     "mka_kernel_launches", "mka_last_error", "mka_status_string",
 ]
 
@@ -108,7 +109,9 @@ def load(path: str | None = None) -> C.CDLL:
         "mka_cg_patch_targets": [P, P, I64, I32, D, P, P, P, P],
         "mka_system_set_warm_start": [P, P],
         "mka_result_copy_warm_start": [P, P],
-        "mka_sweep_create": [P, I64, I64, I32, D, D, I32, I64, P, P],
+        "mka_sweep_create": [P, I64, I64, I32, D, D, I32, I64, I32, P, P],
+        "mka_sweep_forces": [P, P, D, D, P, P],
+        "mka_forces": [P, P, D, D, P, P],
         "mka_sweep_info": [P, P, P, P, P],
         "mka_plan_run_sweep": [P, P, P, I64],
         "mka_sweep_status": [P, P, P],
@@ -372,11 +375,24 @@ def mka_autotune(sys, prm: mka_solve_params, sample: np.ndarray, n_electrons: fl
 # ---- whole-system sweep ------------------------------------------------------------------
 
 def mka_sweep_create(sys, atom_begin: int, atom_end: int, nu: int, win_lo: float, win_hi: float, kp: int,
-                     chunk_atoms: int = 4096, stream: int = 0) -> C.c_void_p:
+                     chunk_atoms: int = 4096, stream: int = 0, with_forces: bool = False) -> C.c_void_p:
     out = C.c_void_p()
     _check(load().mka_sweep_create(sys, int(atom_begin), int(atom_end), int(nu), float(win_lo), float(win_hi), int(kp),
-                                   int(chunk_atoms), C.c_void_p(stream), C.byref(out)), "mka_sweep_create")
+                                   int(chunk_atoms), int(with_forces), C.c_void_p(stream), C.byref(out)),
+           "mka_sweep_create")
     return out
+
+
+def mka_sweep_forces(sw, plan, mu: float, kT: float, forces_ptr: int) -> int:
+    n = C.c_int64()
+    _check(load().mka_sweep_forces(sw, plan, float(mu), float(kT), C.c_void_p(forces_ptr), C.byref(n)),
+           "mka_sweep_forces")
+    return n.value
+
+
+def mka_forces(sys, res, mu: float, kT: float, pi_ptr: int | None = None, forces_ptr: int | None = None):
+    _check(load().mka_forces(sys, res, float(mu), float(kT), C.c_void_p(pi_ptr) if pi_ptr else None,
+                             C.c_void_p(forces_ptr) if forces_ptr else None), "mka_forces")
 
 
 def mka_sweep_info(sw) -> dict:
