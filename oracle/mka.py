@@ -260,3 +260,18 @@ def greens_column(col: Column, z: complex, rows: np.ndarray) -> np.ndarray:
 def column_energy(col: Column, f: np.ndarray, H: np.ndarray, rows: np.ndarray) -> float:
     """E^(j) = sum_i rho_ij H_ji over the selected rows (Eq. EQ-ENE partial sum)."""
     return float(rho_column(col, f, rows) @ H[col.j, rows])
+
+
+def dos(eps: np.ndarray, w: np.ndarray, energies, eta: float) -> np.ndarray:
+    """Density of states from the subspace Green's function (Sec. 3, DOS discussion):
+    D(E) = -(1/pi) Im sum_j (G(E + i eta) S)_jj, with sum_i G_ji(z) S_ij = sum_alpha w_alpha / (z - eps_alpha)
+    for the column's Galerkin pairs (Eq. EQ-SOLUTION-SUB-GZ and w_alpha = v_alpha,j (S v_alpha)_j).
+    `eps`, `w`: every column's levels and weights (entries with w = 0 add nothing). One value per
+    state (no spin factor)."""
+    eps = np.asarray(eps, dtype=np.float64).ravel()
+    w = np.asarray(w, dtype=np.float64).ravel()
+    out = np.empty(len(energies))
+    for k, E in enumerate(energies):
+        z = complex(E, eta)
+        out[k] = -np.imag(np.sum(w / (z - eps))) / np.pi
+    return out
