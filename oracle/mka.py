@@ -92,7 +92,7 @@ class Basis:
 
 
 def multiple_arnoldi_basis(H: np.ndarray, S: np.ndarray, j: int, s: np.ndarray, p: int, q: int,
-                           tau: float = BREAKDOWN_TAU, passes: int = GS_PASSES) -> Basis:
+                           tau: float = BREAKDOWN_TAU, passes: int = GS_PASSES, mode: str = "A") -> Basis:
     """S-orthonormal basis of L_nu^(j) = K_p(H; e_j) (+) K_q(H; s_j) (Sec. 2).
 
     Each new vector l is S-orthogonalised against u_1..u_{n-1} (Eq.
@@ -100,9 +100,17 @@ def multiple_arnoldi_basis(H: np.ndarray, S: np.ndarray, j: int, s: np.ndarray, 
     (Eq. EQ-REC-UN), and k_n = H u_n is formed (Eq. EQ-KN-HUN). The next l is
     k_n, except after u_p where it is s_j (Eq. EQ-CALC-S-INV, seam reading in
     the module docstring). Breakdown handling as in the module docstring.
+
+    mode "B" (the literal direct sum of Eq. EQ-SUBSPACE-MULTI-KRY): after the seam
+    the next vector is H applied to the previous raw vector of the s_j chain
+    (s_j, H s_j, H^2 s_j, ..., each scaled to unit 2-norm), not to the
+    orthogonalised u_n, so the span is exactly K_p(H; e_j) + K_q(H; s_j). A raw
+    vector that breaks down ends the basis (it and every later power lie in the span).
     """
     if p < 1 or q < 0:
         raise OracleError("need p >= 1 and q >= 0")
+    if mode not in ("A", "B"):
+        raise OracleError("mode is 'A' or 'B'")
     m = H.shape[0]
     nu = p + q
     U, SU, K = [], [], []
@@ -112,6 +120,7 @@ def multiple_arnoldi_basis(H: np.ndarray, S: np.ndarray, j: int, s: np.ndarray, 
     seam_done = q == 0
     seam_at = 0
     substituted = False
+    raw = None                     # mode B: the current raw vector of the s_j chain
     n = 0
     while n < nu:
         beta_pre = np.sqrt(max(l @ (S @ l), 0.0))
@@ -122,6 +131,8 @@ def multiple_arnoldi_basis(H: np.ndarray, S: np.ndarray, j: int, s: np.ndarray, 
         Sl = S @ l
         beta = np.sqrt(max(l @ Sl, 0.0))
         if not beta > tau * beta_pre:
+            if src == "r":
+                break
             if src == "s":
                 # s_j already lies in the span: continue the first chain with H u_n.
                 l = K[n - 1].copy()
@@ -142,7 +153,12 @@ def multiple_arnoldi_basis(H: np.ndarray, S: np.ndarray, j: int, s: np.ndarray, 
         SU.append(Sl / beta)
         K.append(H @ u)                # Eq. EQ-KN-HUN
         n += 1
-        if n == p and not seam_done:
+        if mode == "B" and src in ("s", "r"):
+            raw = H @ (s if src == "s" else raw)   # the next power of the s_j chain, from the raw vector
+            raw = raw / np.linalg.norm(raw)
+            l = raw.copy()
+            src = "r"
+        elif n == p and not seam_done:
             l = s.copy()               # Eq. EQ-CALC-S-INV: the next vector is s_j
             src = "s"
             seam_done = True
@@ -200,12 +216,12 @@ class Column:
 
 
 def solve_column(H: np.ndarray, S: np.ndarray, j: int, p: int, q: int, cg_tol: float = 1e-13,
-                 x0: np.ndarray | None = None) -> Column:
+                 x0: np.ndarray | None = None, mode: str = "A") -> Column:
     """One column of the work flow, Eq. EQ-WORK-FLOW first brace: {u_n} => {v_alpha, eps_alpha}."""
     e = np.zeros(H.shape[0])
     e[j] = 1.0
     s, it = cg(S, e, tol=cg_tol, x0=x0)
-    B = multiple_arnoldi_basis(H, S, j, s, p, q)
+    B = multiple_arnoldi_basis(H, S, j, s, p, q, mode=mode)
     R = reduced_problem(B)
     V = B.U @ R.C
     SV = B.SU @ R.C

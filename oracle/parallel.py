@@ -14,19 +14,20 @@ from . import system as osys
 
 
 def _work(args):
-    pos, box, skp, R, atoms, p, q, storage, cg_tol = args
-    return [osys.solve_atom(pos, box, skp, R, int(a), p, q, storage, cg_tol) for a in atoms]
+    pos, box, skp, R, atoms, p, q, storage, cg_tol = args[:9]
+    mode = args[9] if len(args) > 9 else "A"
+    return [osys.solve_atom(pos, box, skp, R, int(a), p, q, storage, cg_tol, mode=mode) for a in atoms]
 
 
-def solve_atoms_parallel(pos, box, skp, R, atoms, p, q, storage="fp64", cg_tol=1e-13, workers=None):
+def solve_atoms_parallel(pos, box, skp, R, atoms, p, q, storage="fp64", cg_tol=1e-13, workers=None, mode="A"):
     atoms = list(np.asarray(atoms, dtype=np.int64))
     workers = workers or min(16, os.cpu_count() or 1)
     if len(atoms) <= 4 or workers == 1:
-        return _work((pos, box, skp, R, atoms, p, q, storage, cg_tol))
+        return _work((pos, box, skp, R, atoms, p, q, storage, cg_tol, mode))
     chunks = [atoms[i::workers] for i in range(workers)]
     chunks = [c for c in chunks if c]
     ctx = mp.get_context("spawn")
     with ctx.Pool(len(chunks)) as pool:
-        parts = pool.map(_work, [(pos, box, skp, R, c, p, q, storage, cg_tol) for c in chunks])
+        parts = pool.map(_work, [(pos, box, skp, R, c, p, q, storage, cg_tol, mode) for c in chunks])
     by_atom = {r.atom: r for part in parts for r in part}
     return [by_atom[int(a)] for a in atoms]

@@ -57,7 +57,7 @@ class AtomResult:
 
 
 def solve_atom(pos: np.ndarray, box: np.ndarray, skp, R: float, a: int, p: int, q: int,
-               storage: str = "fp64", cg_tol: float = 1e-13, keep_full: bool = False) -> AtomResult:
+               storage: str = "fp64", cg_tol: float = 1e-13, keep_full: bool = False, mode: str = "A") -> AtomResult:
     cl = skmod.cluster_atoms(pos, box, a, R)
     Hc, Sc = skmod.cluster_matrices(pos, box, cl, skp)
     Hc = round_storage(Hc, storage)
@@ -67,7 +67,7 @@ def solve_atom(pos: np.ndarray, box: np.ndarray, skp, R: float, a: int, p: int, 
     loc = np.minimum(np.searchsorted(cl, nb), len(cl) - 1)
     inside = np.repeat(cl[loc] == nb, 4)        # pattern atoms beyond R lie outside the projection
     rows = (4 * loc[:, None] + np.arange(4)[None, :]).ravel()
-    cols = [mka.solve_column(Hc, Sc, 4 * t + o, p, q, cg_tol=cg_tol) for o in range(4)]
+    cols = [mka.solve_column(Hc, Sc, 4 * t + o, p, q, cg_tol=cg_tol, mode=mode) for o in range(4)]
     # v_alpha lives on the cluster: its rows outside the cluster are zero.
     data = [ColumnData(c.eps, c.w, c.V[rows, :] * inside[:, None], c.V[c.j, :], c.cg_iters, c.basis.nu_eff)
             for c in cols]
@@ -75,8 +75,9 @@ def solve_atom(pos: np.ndarray, box: np.ndarray, skp, R: float, a: int, p: int, 
     return AtomResult(a, cl, nb, rows, Hrow, data, p + q, cols if keep_full else None)
 
 
-def solve_atoms(pos, box, skp, R, atoms, p, q, storage="fp64", cg_tol=1e-13, keep_full=True) -> list[AtomResult]:
-    return [solve_atom(pos, box, skp, R, int(a), p, q, storage, cg_tol, keep_full) for a in atoms]
+def solve_atoms(pos, box, skp, R, atoms, p, q, storage="fp64", cg_tol=1e-13, keep_full=True,
+                mode="A") -> list[AtomResult]:
+    return [solve_atom(pos, box, skp, R, int(a), p, q, storage, cg_tol, keep_full, mode) for a in atoms]
 
 
 def stack_eps_w(results: list[AtomResult]) -> tuple[np.ndarray, np.ndarray]:

@@ -375,3 +375,29 @@ def test_second_chain_pin_catches_h_on_s():
     ref = galerkin_rho(H, S, W, j, mu, kT)
     planted = galerkin_rho(H, S, reading_b_subspace(H, S, j, p, q), j, mu, kT)
     assert np.abs(planted - ref).max() > 1e-6
+
+
+@pytest.mark.parametrize("p,q,seed", [(3, 2, 41), (4, 3, 42), (5, 5, 43)])
+def test_reading_b_is_the_direct_sum(p, q, seed):
+    """mode "B": the oracle's basis spans exactly K_p(H; e_j) + K_q(H; s_j) (explicit Krylov matrices of
+    e_j and of s_j, QR of their union): eps, rho and G of the Galerkin problem match at 1e-10, and differ
+    from reading A's."""
+    m = 40
+    H, S = random_symmetric_pair(m, seed)
+    j, mu, kT, z = 5, 0.1, 0.25, 0.3 + 0.4j
+    col = mka.solve_column(H, S, j, p, q, mode="B")
+    assert col.basis.nu_eff == p + q
+    Qw, _ = np.linalg.qr(reading_b_subspace(H, S, j, p, q))
+    e, Y = scipy.linalg.eigh(Qw.T @ H @ Qw, Qw.T @ S @ Qw)
+    Vg = Qw @ Y
+    rows = np.arange(m)
+    f = mka.fermi(col.eps, mu, kT)
+    np.testing.assert_allclose(col.eps, e, atol=1e-10)
+    np.testing.assert_allclose(mka.rho_column(col, f, rows), Vg @ (mka.fermi(e, mu, kT) * Vg[j, :]), atol=1e-10)
+    np.testing.assert_allclose(mka.greens_column(col, z, rows), Vg @ (Vg[j, :] / (z - e)), atol=1e-10)
+    cA = mka.solve_column(H, S, j, p, q, mode="A")
+    assert np.abs(mka.rho_column(cA, mka.fermi(cA.eps, mu, kT), rows) - mka.rho_column(col, f, rows)).max() > 1e-6
+    # the identities that hold for any subspace containing e_j and s_j hold for B as well
+    assert abs(col.w.sum() - 1.0) < 1e-12
+    np.testing.assert_allclose(mka.rho_column(col, np.ones_like(col.eps), rows), np.linalg.solve(S, np.eye(m)[:, j]),
+                               atol=1e-11)
