@@ -27,7 +27,18 @@ def solve_atoms_parallel(pos, box, skp, R, atoms, p, q, storage="fp64", cg_tol=1
     chunks = [atoms[i::workers] for i in range(workers)]
     chunks = [c for c in chunks if c]
     ctx = mp.get_context("spawn")
-    with ctx.Pool(len(chunks)) as pool:
-        parts = pool.map(_work, [(pos, box, skp, R, c, p, q, storage, cg_tol, mode) for c in chunks])
+    # one BLAS thread per worker process (the workers already fill the cores); the children inherit this
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        with ctx.Pool(len(chunks)) as pool:
+            parts = pool.map(_work, [(pos, box, skp, R, c, p, q, storage, cg_tol, mode) for c in chunks])
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     by_atom = {r.atom: r for part in parts for r in part}
     return [by_atom[int(a)] for a in atoms]

@@ -57,9 +57,13 @@ class AtomResult:
 
 
 def solve_atom(pos: np.ndarray, box: np.ndarray, skp, R: float, a: int, p: int, q: int,
-               storage: str = "fp64", cg_tol: float = 1e-13, keep_full: bool = False, mode: str = "A") -> AtomResult:
+               storage: str = "fp64", cg_tol: float = 1e-13, keep_full: bool = False, mode: str = "A",
+               onsite_shift: np.ndarray | None = None) -> AtomResult:
+    """`onsite_shift` [N] (eV) is added to the diagonal of every atom's on-site H block (a CSC potential)."""
     cl = skmod.cluster_atoms(pos, box, a, R)
     Hc, Sc = skmod.cluster_matrices(pos, box, cl, skp)
+    if onsite_shift is not None:
+        Hc = Hc + np.diag(np.repeat(np.asarray(onsite_shift)[cl], 4))
     Hc = round_storage(Hc, storage)
     Sc = round_storage(Sc, storage)
     t = int(np.searchsorted(cl, a))
