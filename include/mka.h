@@ -66,8 +66,10 @@ typedef enum {
 
 /* Largest cluster a column may have (atoms). m_c = 4 x atoms <= 2048. */
 #define MKA_MAX_CLUSTER_ATOMS 512
-/* Largest subspace dimension nu = p + q. */
-#define MKA_MAX_NU 64
+/* Largest subspace dimension nu = p + q (the density of states, an energy-resolved
+ * quantity, wants subspaces of a few hundred: Sec. 3). Subspaces above 64 run the
+ * batched reduced problems with larger per-column buffers. */
+#define MKA_MAX_NU 320
 
 typedef struct mka_system mka_system; /* device BSR H and S, positions, cell list */
 typedef struct mka_result mka_result; /* per-column levels, weights, status, kept vectors */
@@ -100,7 +102,23 @@ typedef struct {
                          the row V_j = (row j of U) C (nu^2 + nu doubles), since
                          sum_alpha x_alpha v_alpha,i v_alpha,j = U_i . (C diag(x) V_j);
                          0: keep only (eps, w) */
+  int keep_s;         /* 1: the result keeps every column's s_j = S^{-1} e_j on its cluster (FP64, 16 doubles
+                         and 1 int per cluster atom and selected atom) for a later solve's s_start */
+  const mka_result* s_start; /* NULL, or an earlier result of mka_solve_columns with keep_s = 1 for the
+                         same atoms in the same order, possibly of another system with the same atom
+                         numbering (atoms moved by an MD step): the inner CG starts from that s_j,
+                         matched by atom id onto the new cluster. With S unchanged (a charge-self-
+                         consistent loop changes only H, Sec. 2) CG is already converged. Direct solves
+                         only (not plans) */
+  int subspace;       /* MKA_SUBSPACE_A (0): the vector after u_p is s_j and H keeps acting on the
+                         latest u_n (span K_p(H; e_j) + K_q((I - Pi_p) H; (I - Pi_p) s_j), Pi_p the
+                         S-orthogonal projector onto K_p(H; e_j)); MKA_SUBSPACE_B (1): the literal
+                         direct sum K_p(H; e_j) + K_q(H; s_j) of Eq. EQ-SUBSPACE-MULTI-KRY, the s_j
+                         chain continued from its raw vectors H^k s_j (q more H products) */
 } mka_solve_params;
+
+#define MKA_SUBSPACE_A 0
+#define MKA_SUBSPACE_B 1
 
 /* ---- system ------------------------------------------------------------ */
 
@@ -126,6 +144,12 @@ mka_status mka_build_system_bsr(const double* pos, int64_t n_atoms, const double
                                 const int32_t* row_ptr, const int32_t* col, int64_t nnzb,
                                 const double* valH, const double* valS, int storage,
                                 double cluster_radius, void* stream, mka_system** out);
+
+/* Add shift[a] (host double [n_atoms], eV) to the diagonal of atom a's on-site block of H, in
+ * place: the on-site potential a charge-self-consistent loop updates between solves while S and
+ * the positions stay fixed (Sec. 2, CSC remark; keep_s / s_start then reuse every s_j). The
+ * stored value is decoded, shifted and rounded back to the storage format. Synchronises. */
+mka_status mka_system_shift_onsite(mka_system* sys, const double* shift, void* stream);
 
 /* Sizes: atoms, blocks, stored precision. Any output pointer may be NULL. */
 mka_status mka_system_info(const mka_system* sys, int64_t* n_atoms, int64_t* nnzb,
@@ -261,6 +285,17 @@ mka_status mka_greens(mka_system* sys, mka_result* res, double z_re, double z_im
  * and a system built by mka_build_system (MKA_ERR_INVALID_ARG otherwise). */
 mka_status mka_forces(mka_system* sys, mka_result* res, double mu, double kT, double* pi_out, double* forces);
 
+/* Density of states from the subspace Green's function (Sec. 3):
+ *   D(E) = -(1/pi) Im sum_j (G(E + i eta) S)_jj = (eta / pi) sum_j sum_alpha w_alpha / ((E - eps_alpha)^2 + eta^2),
+ * since sum_i G_ji(z) S_ij = sum_alpha w_alpha / (z - eps_alpha) for each column's Galerkin pairs.
+ *   eps, w    device double [n_levels]: any columns' levels and weights, flattened (for example a
+ *             result's or a sweep's [n_cols][nu] arrays; entries with w = 0 add nothing)
+ *   energies  host double [n_energies]; eta > 0 the broadening (eV)
+ *   dos       host double [n_energies] out, states per eV (one per state, no spin factor)
+ * FP64, fixed summation order; synchronises `stream`. */
+mka_status mka_dos(const double* eps, const double* w, int64_t n_levels, const double* energies, int n_energies,
+                   double eta, void* stream, double* dos);
+
 /* ---- learned warm start for the inner CG ---------------------------------- */
 /* The inner CG for s_j = S^{-1} e_j (Sec. 2) may start from any x0. A small
  * network predicts x0 on the 17-atom patch around j's atom (the atom and its 16
@@ -371,6 +406,16 @@ void mka_plan_destroy(mka_plan* plan);
  * stored there after a search. */
 mka_status mka_autotune(mka_system* sys, const mka_solve_params* prm, const int64_t* sample, int64_t n_sample,
                         double n_electrons, double kT, const char* cache_path, void* stream, mka_tuning* out);
+
+/* Choose the batch size of plans for `prm` and launch shape `tune` (NULL = defaults): each candidate
+ * (host array, atoms per batch) that fits runs a batch of consecutive atoms from first_atom through a
+ * plan twice; the highest columns/s of the second run wins, into *out_batch. With `cache_path` the
+ * choice is looked up first and stored after a search (key: GPU, storage, arithmetic, p + q, subspace,
+ * system size, launch shape, candidates). MKA_ERR_OOM when no candidate fits. */
+mka_status mka_autotune_batch(mka_system* sys, const mka_solve_params* prm, const mka_tuning* tune,
+                              const int64_t* candidates, int n_candidates, int64_t first_atom,
+                              double electrons_per_atom, double kT, const char* cache_path, void* stream,
+                              int64_t* out_batch);
 
 /* ---- whole-system sweep: every column, one mu, then rho ------------------ */
 

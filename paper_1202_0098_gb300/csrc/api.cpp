@@ -63,6 +63,8 @@ void mka_result_destroy(mka_result* r) {
   cudaFree(r->d_cv);
   cudaFree(r->d_mu_state);
   cudaFree(r->d_fallback);
+  cudaFree(r->d_s_cl);
+  cudaFree(r->d_s);
   delete r;
 }
 
@@ -76,8 +78,21 @@ mka_status mka_solve_columns(mka_system* sys, const int64_t* atoms, int64_t n_se
   if (prm->arith != MKA_FP64 && prm->arith != MKA_MIXED_FP32)
     return fail(MKA_ERR_INVALID_ARG, "arith must be MKA_FP64 or MKA_MIXED_FP32");
   if (!(prm->cg_tol > 0) || prm->cg_maxit < 1) return fail(MKA_ERR_INVALID_ARG, "need cg_tol > 0, cg_maxit >= 1");
+  if (prm->subspace != MKA_SUBSPACE_A && prm->subspace != MKA_SUBSPACE_B)
+    return fail(MKA_ERR_INVALID_ARG, "subspace must be MKA_SUBSPACE_A or MKA_SUBSPACE_B");
   if (prm->use_warm_start && !sys->warm)
     return fail(MKA_ERR_INVALID_ARG, "use_warm_start needs a network attached with mka_system_set_warm_start");
+  if (prm->use_warm_start && prm->s_start)
+    return fail(MKA_ERR_INVALID_ARG, "use_warm_start and s_start are exclusive CG starts");
+  if (prm->s_start) {
+    const mka_result* pr = prm->s_start;
+    if (!pr->d_s) return fail(MKA_ERR_INVALID_ARG, "s_start was solved without keep_s");
+    if (!pr->sys || pr->sys->n_atoms != sys->n_atoms) return fail(MKA_ERR_INVALID_ARG, "s_start belongs to a system of another size");
+    const int64_t n = atoms ? n_sel : sys->n_atoms;
+    if (pr->n_sel != n) return fail(MKA_ERR_INVALID_ARG, "s_start has another selection");
+    for (int64_t t = 0; t < n; ++t)
+      if (pr->h_sel[t] != (atoms ? atoms[t] : t)) return fail(MKA_ERR_INVALID_ARG, "s_start has another selection");
+  }
   cudaStream_t st = (cudaStream_t)stream;
   mka_result* r = new mka_result();
   r->sys = sys;
@@ -139,6 +154,15 @@ mka_status mka_solve_columns(mka_system* sys, const int64_t* atoms, int64_t n_se
     return s != MKA_OK ? s : cuda_fail(e, "cluster sizes");
   }
   const int max_cl = *std::max_element(sizes.begin(), sizes.end());
+  if (prm->keep_s) {
+    r->s_cap = std::max(1, std::min(max_cl, MKA_MAX_CLUSTER_ATOMS));
+    e = cudaMalloc(&r->d_s_cl, sizeof(int32_t) * r->n_sel * r->s_cap);
+    if (e == cudaSuccess) e = cudaMalloc(&r->d_s, sizeof(double) * 16 * r->n_sel * r->s_cap);
+    if (e != cudaSuccess) {
+      mka_result_destroy(r);
+      return cuda_fail(e, "keep_s allocation");
+    }
+  }
   s = launch_columns(sys, r, prm, max_cl, st);
   if (s != MKA_OK) {
     mka_result_destroy(r);
@@ -271,6 +295,21 @@ mka_status mka_greens(mka_system* sys, mka_result* r, double z_re, double z_im, 
   if (!sys || !r || r->sys != sys || !g_out) return fail(MKA_ERR_INVALID_ARG, "system, result and g_out are required");
   if (!r->keep) return fail(MKA_ERR_INVALID_ARG, "greens needs a result solved with keep_vectors = 1");
   return launch_greens(sys, r, z_re, z_im, g_out);
+}
+
+mka_status mka_system_shift_onsite(mka_system* sys, const double* shift, void* stream) {
+  if (!sys || !shift) return fail(MKA_ERR_INVALID_ARG, "system and shift are required");
+  for (int64_t a = 0; a < sys->n_atoms; ++a)
+    if (!std::isfinite(shift[a])) return fail(MKA_ERR_INVALID_ARG, "shifts must be finite");
+  return launch_onsite_shift(sys, shift, (cudaStream_t)stream);
+}
+
+mka_status mka_dos(const double* eps, const double* w, int64_t n_levels, const double* energies, int n_energies,
+                   double eta, void* stream, double* dos) {
+  if (!eps || !w || !energies || !dos || n_levels < 1 || n_energies < 1)
+    return fail(MKA_ERR_INVALID_ARG, "levels, weights, energies and dos are required (n >= 1)");
+  if (!(eta > 0)) return fail(MKA_ERR_INVALID_ARG, "need eta > 0");
+  return launch_dos(eps, w, n_levels, energies, n_energies, eta, (cudaStream_t)stream, dos);
 }
 
 mka_status mka_spmv(const mka_system* sys, int which, int x_dtype, const void* x, void* y, int k, void* stream) {

@@ -14,6 +14,8 @@
 //      EQ-REC-UN, EQ-KN-HUN, EQ-MGram-Schmidt, EQ-CALC-S-INV); Gram-Schmidt is
 //      one classical pass, coefficients (S u_m)^T l with S u_m kept, corrected to
 //      first order by S_r - I (the seam vector gets two full FP64 passes);
+//      optionally the s_j chain continues from its raw vectors H^k s_j (the
+//      literal direct sum, reading B);
 //   4. the projection H_r = U^T K, S_r = U^T (S U), accumulated while the basis
 //      grows, written with row j of U and S U to the reduced-problem buffer;
 //      the reduced generalized problem (Eq. EQ-SUB-EIG-VEC) and the per-column
@@ -25,11 +27,11 @@
 // coefficients) is dropped; a dropped s_j is replaced by H u_n, a first chain
 // that closes before u_p hands over to s_j, any other breakdown ends the basis.
 //
-// The work vectors (CG: p, S p, r; basis: l, S l, H u) live in shared memory,
-// [row][4 columns] interleaved so that one thread owns a row of all four
-// columns; the basis U and S U, s_j and the projected matrices live in a
-// per-CTA global slot. Arithmetic type T is double for the FP64 form and float
-// for the mixed form (values of any storage type are decoded to T on load).
+// The vector the SpMV gathers (CG: p; basis: l) lives in shared memory, [row][4 columns]
+// interleaved so that one thread owns a row of all four columns; the basis U and S U, s_j,
+// the streamed work vectors and S_r - I live in a per-CTA global slot. Arithmetic type T is
+// double for the FP64 form and float for the mixed form (values of any storage type are
+// decoded to T on load).
 //
 // Mixed form. s_j is nearly inside K_p(H; e_j): the seam vector keeps about 1%
 // of its S-norm, so any perturbation of the first chain at FP32 rounding level
@@ -64,7 +66,7 @@ __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + 
 
 enum ColStatus { ST_OK = 0, ST_NOT_SPD = MKA_ERR_NOT_SPD, ST_NOCONV = MKA_ERR_NO_CONVERGENCE,
                  ST_BREAKDOWN = MKA_ERR_BREAKDOWN, ST_TOOLARGE = MKA_ERR_CLUSTER_TOO_LARGE };
-enum Src { SRC_E = 0, SRC_H = 1, SRC_S = 2 };
+enum Src { SRC_E = 0, SRC_H = 1, SRC_S = 2, SRC_R = 3 };   // SRC_R: a raw power H^k s_j (reading B)
 enum Act { ACT_NONE = 0, ACT_LOAD_K = 1, ACT_LOAD_S = 2 };
 
 // ---- value loads: one row (4 entries) of a 4x4 block, decoded ----------------
@@ -144,6 +146,17 @@ struct Args {
   // CG-only mode: stop after the inner CG and write s_j on the patch (training targets)
   int cg_only;
   float* cg_target;         // [4 n_sel][68]
+  // 1: the s_j chain continues from its raw vector (the literal direct sum K_p(H; e_j) + K_q(H; s_j))
+  int mode_b;
+  // s_j of an earlier solve of the same atoms as the CG start: its clusters' atom ids [n_sel][prev_cap]
+  // (ascending, -1 beyond the count) and values [4 n_sel][4 prev_cap] (NULL: not used)
+  const int32_t* prev_cl;
+  const double* prev_s;
+  int prev_cap;
+  // keep this solve's s_j the same way (NULL: not kept), keep_cap atoms per cluster
+  int32_t* keep_cl;
+  double* keep_s;
+  int keep_cap;
   double* red;              // reduced-problem buffer, lane-interleaved per 32 columns
 };
 
@@ -527,7 +540,7 @@ __device__ __forceinline__ void dot4(const T* a, const T* b, int m, double* red,
 
 // ---- shared state of one atom --------------------------------------------------------
 struct AtomState {
-  int n[4], src[4], seam_done[4], active[4], accept[4], act[4], next_s[4], proj[4];
+  int n[4], src[4], seam_done[4], active[4], accept[4], act[4], next_s[4], proj[4], next_raw[4];
   int it[4], cg_active[4], status[4];
   double beta_inv[4], csum[4], rr[4], alpha[4], beta_cg[4], cg_stop[4];
   int ncl, t0, flag, n_max, proj_any, acc_mask, act_mask;
@@ -596,6 +609,122 @@ __device__ void gs_sweep(const T* U, const T* SU, const T* L, const T* KV, const
   __syncthreads();
 }
 
+// The seam vector of the FP32 form in FP64: two classical Gram-Schmidt passes on s_j (FP64, in place)
+// against the basis pairs for the columns in smask, the result left in l as a pair. Kept out of line:
+// it runs once per atom, and inlined it would crowd the instruction cache of the basis loop.
+__device__ __noinline__ void seam_fp64(const float* SU, const float* U, const float* Ulo, double* SJd, float* Lv,
+                                       float* Llo, double* coef, AtomState& st, int m, int m_cap, int nmax, int smask) {
+  using T = float;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  if (threadIdx.x < 4) st.csum[threadIdx.x] = (smask >> threadIdx.x & 1) ? 0.0 : st.csum[threadIdx.x];
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int mm = wid; mm < nmax; mm += nwarp) {
+      const T* su = SU + (size_t)mm * m_cap * 4;
+      double acc[4] = {0, 0, 0, 0};
+      for (int r = lane; r < m; r += 32)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (smask >> q & 1) acc[q] += (double)su[4 * r + q] * SJd[4 * r + q];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = warp_sum(acc[q]);
+      if (lane < 4) coef[mm * 4 + lane] = ((smask >> lane & 1) && mm < st.n[lane]) ? acc[lane] : 0.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
+      const int r = i >> 2, q = i & 3;
+      if (!(smask >> q & 1)) continue;
+      double v = SJd[i];
+      for (int mm = 0; mm < nmax; ++mm) {
+        const size_t o = (size_t)mm * m_cap * 4 + 4 * r + q;
+        const double cf = coef[mm * 4 + q];
+        if (cf != 0.0) v -= cf * ((double)U[o] + (double)Ulo[o]);
+      }
+      SJd[i] = v;
+    }
+    if (threadIdx.x < 4 && (smask >> threadIdx.x & 1)) {
+      double s2 = 0;
+      for (int mm = 0; mm < nmax; ++mm) s2 += coef[mm * 4 + threadIdx.x] * coef[mm * 4 + threadIdx.x];
+      st.csum[threadIdx.x] += s2;
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < 4 * m; i += blockDim.x)
+    if (smask >> (i & 3) & 1) {
+      const T h = (T)SJd[i];
+      Lv[i] = h;
+      Llo[i] = (float)(SJd[i] - (double)h);
+    }
+  __syncthreads();
+}
+
+// s_j dropped as already in the span (columns in kmask): l becomes u_n, the last accepted vector, and
+// KV = H u_n is formed again (KV held H applied to the dropped s_j). Kept out of line: it runs at most
+// once per column, and inlined its product would crowd the instruction cache of the basis loop.
+template <typename TV, typename T>
+__device__ __noinline__ void reload_hu(const TV* __restrict__ valH, const int* lrow, const uint16_t* lcol,
+                                       const int* rbase, const uint8_t* loff, int ncl, int m, int m_cap, int kmask,
+                                       const AtomState& st, const T* U, const float* Ulo, T* Lv, float* Llo, T* KV,
+                                       float* Klo) {
+  for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
+    const int r = i >> 2, c = i & 3;
+    if (!(kmask >> c & 1)) continue;
+    const size_t o = (size_t)(st.n[c] - 1) * m_cap * 4 + 4 * r + c;
+    Lv[i] = U[o];
+    if constexpr (sizeof(T) == 4) Llo[i] = Ulo[o];
+  }
+  __syncthreads();
+  if constexpr (sizeof(T) == 4)
+    spmm4_pair<TV>(valH, lrow, lcol, rbase, loff, ncl, Lv, Llo, KV, Klo, kmask);
+  else
+    spmm4<TV, T>(valH, lrow, lcol, rbase, loff, ncl, Lv, KV, kmask);
+}
+
+// Reading B: the next raw vector of the s_j chain for the columns in rmask, H applied to s_j (columns in
+// pmask, copied from s_j first) or to the previous raw vector, scaled by a power of two near its inverse
+// 2-norm (exact for both halves of a pair); left in RW (and RWlo). Kept out of line: it runs a few times
+// per atom, and inlined its products would crowd the instruction cache of the basis loop.
+template <typename TV, typename T>
+__device__ __noinline__ void raw_chain_step(const TV* __restrict__ valH, const int* lrow, const uint16_t* lcol,
+                                            const int* rbase, const uint8_t* loff, int ncl, int m, int pmask, int rmask,
+                                            const T* SJ, const double* SJd, T* RW, T* RWN, float* RWlo, float* RWNlo,
+                                            double* red, double* sums, T* scal) {
+  for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
+    const int c = i & 3;
+    if (!(pmask >> c & 1)) continue;
+    if constexpr (sizeof(T) == 4) {
+      const float h = (float)SJd[i];
+      RW[i] = h;
+      RWlo[i] = (float)(SJd[i] - (double)h);
+    } else {
+      RW[i] = SJ[i];
+    }
+  }
+  __syncthreads();
+  if constexpr (sizeof(T) == 4)
+    spmm4_pair<TV>(valH, lrow, lcol, rbase, loff, ncl, reinterpret_cast<const float*>(RW), RWlo,
+                   reinterpret_cast<float*>(RWN), RWNlo, rmask);
+  else
+    spmm4<TV, T>(valH, lrow, lcol, rbase, loff, ncl, RW, RWN, rmask);
+  dot4<T>(RWN, RWN, m, red, sums);
+  if (threadIdx.x < 4) {
+    const int c = threadIdx.x;
+    scal[c] = (T)1;
+    if (rmask >> c & 1) {
+      const double nrm = sqrt(fmax(sums[c], 0.0));
+      scal[c] = nrm > 0.0 ? (T)ldexp(1.0, -ilogb(nrm)) : (T)1;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
+    const int c = i & 3;
+    if (!(rmask >> c & 1)) continue;
+    RW[i] = RWN[i] * scal[c];
+    if constexpr (sizeof(T) == 4) RWlo[i] = RWNlo[i] * (float)scal[c];
+  }
+  __syncthreads();
+}
+
 template <typename TV, typename T, int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -641,6 +770,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
   float* Klo = reinterpret_cast<float*>(V2 + (size_t)m_cap * 4);
   float* Ulo = Klo + (size_t)m_cap * 4;
   (void)Ulo;
+  // reading B: the raw vector of the s_j chain and H applied to it, [m_cap][4] each (with low halves in
+  // the FP32 form)
+  T* RW = reinterpret_cast<T*>(reinterpret_cast<char*>(V2 + (size_t)m_cap * 4) +
+                               align_up(sizeof(T) == 4 ? sizeof(float) * ((size_t)nu + 1) * m_cap * 4 : 0, 256));
+  T* RWN = RW + (size_t)m_cap * 4;
+  float* RWlo = reinterpret_cast<float*>(RWN + (size_t)m_cap * 4);
+  float* RWNlo = RWlo + (size_t)m_cap * 4;
   (void)Llo;
   (void)Klo;
 
@@ -734,15 +870,40 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
       st.act[c] = 0;    // reused: warm-start fallback flag
     }
     __syncthreads();
-    if (A.x0) {
-      for (int i = threadIdx.x; i < 4 * 68; i += blockDim.x) {   // (column, patch atom, orbital)
-        const int c = i / 68, rem = i % 68, k = rem >> 2, o = rem & 3;
-        const int pa = A.patch[widx * 17 + k];
-        const int lk = pa >= 0 ? find_local(cl, ncl, pa) : -1;
-        if (lk < 0) continue;
-        const T v = (T)A.x0[(4 * widx + c) * 68 + rem];
-        SJ[4 * (4 * lk + o) + c] = v;
-        P[4 * (4 * lk + o) + c] = v;
+    if (A.keep_cl)
+      for (int t = threadIdx.x; t < A.keep_cap; t += blockDim.x) A.keep_cl[widx * A.keep_cap + t] = t < ncl ? cl[t] : -1;
+    if (A.x0 || A.prev_s) {
+      if (A.prev_s) {   // an earlier s_j on this atom's cluster, matched by atom id (atoms new to the cluster start at 0)
+        const int32_t* pc = A.prev_cl + widx * A.prev_cap;
+        int np = 0;
+        while (np < A.prev_cap && pc[np] >= 0) ++np;
+        for (int t = threadIdx.x; t < ncl; t += blockDim.x) {
+          int lo = 0, hi = np - 1, f = -1;
+          while (lo <= hi) {
+            const int mid = (lo + hi) >> 1;
+            if (pc[mid] == cl[t]) { f = mid; break; }
+            if (pc[mid] < cl[t]) lo = mid + 1; else hi = mid - 1;
+          }
+          if (f < 0) continue;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+              const T v = (T)A.prev_s[(4 * widx + c) * (4 * (int64_t)A.prev_cap) + 4 * f + o];
+              SJ[4 * (4 * t + o) + c] = v;
+              P[4 * (4 * t + o) + c] = v;
+            }
+        }
+      } else {
+        for (int i = threadIdx.x; i < 4 * 68; i += blockDim.x) {   // (column, patch atom, orbital)
+          const int c = i / 68, rem = i % 68, k = rem >> 2, o = rem & 3;
+          const int pa = A.patch[widx * 17 + k];
+          const int lk = pa >= 0 ? find_local(cl, ncl, pa) : -1;
+          if (lk < 0) continue;
+          const T v = (T)A.x0[(4 * widx + c) * 68 + rem];
+          SJ[4 * (4 * lk + o) + c] = v;
+          P[4 * (4 * lk + o) + c] = v;
+        }
       }
       __syncthreads();
       spmm4<TV, T>(A.valS, lrow, lcol, rbase, loff, ncl, P, AP, 15);
@@ -877,6 +1038,13 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
       for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) SJ[i] = (T)SJd[i];
     __syncthreads();
     if (A.fallback && threadIdx.x < 4) A.fallback[4 * widx + threadIdx.x] = st.act[threadIdx.x];
+    if (A.keep_s)
+      for (int i = threadIdx.x; i < 16 * A.keep_cap; i += blockDim.x) {   // (column, cluster atom, orbital)
+        const int c = i / (4 * A.keep_cap), rem = i % (4 * A.keep_cap), t = rem >> 2, o = rem & 3;
+        double v = 0.0;
+        if (t < ncl) v = sizeof(T) == 4 ? SJd[4 * (4 * t + o) + c] : (double)SJ[4 * (4 * t + o) + c];
+        A.keep_s[(4 * widx + c) * (4 * (int64_t)A.keep_cap) + rem] = v;
+      }
     if (A.cg_only) {
       for (int i = threadIdx.x; i < 4 * 68; i += blockDim.x) {
         const int c = i / 68, rem = i % 68, k = rem >> 2, o = rem & 3;
@@ -985,49 +1153,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
         // whose l is s_j, replacing what the FP32 pass above made of them
         const int smask = (st.active[0] && st.src[0] == SRC_S) | ((st.active[1] && st.src[1] == SRC_S) << 1) |
                           ((st.active[2] && st.src[2] == SRC_S) << 2) | ((st.active[3] && st.src[3] == SRC_S) << 3);
-        if (smask && nmax > 0) {
-          const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-          if (threadIdx.x < 4) st.csum[threadIdx.x] = (smask >> threadIdx.x & 1) ? 0.0 : st.csum[threadIdx.x];
-          __syncthreads();
-          for (int pass = 0; pass < 2; ++pass) {
-            for (int mm = wid; mm < nmax; mm += nwarp) {
-              const T* su = SU + (size_t)mm * m_cap * 4;
-              double acc[4] = {0, 0, 0, 0};
-              for (int r = lane; r < m; r += 32)
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                  if (smask >> q & 1) acc[q] += (double)su[4 * r + q] * SJd[4 * r + q];
-#pragma unroll
-              for (int q = 0; q < 4; ++q) acc[q] = warp_sum(acc[q]);
-              if (lane < 4) coef[mm * 4 + lane] = ((smask >> lane & 1) && mm < st.n[lane]) ? acc[lane] : 0.0;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
-              const int r = i >> 2, q = i & 3;
-              if (!(smask >> q & 1)) continue;
-              double v = SJd[i];
-              for (int mm = 0; mm < nmax; ++mm) {
-                const size_t o = (size_t)mm * m_cap * 4 + 4 * r + q;
-                const double cf = coef[mm * 4 + q];
-                if (cf != 0.0) v -= cf * ((double)U[o] + (double)Ulo[o]);
-              }
-              SJd[i] = v;
-            }
-            if (threadIdx.x < 4 && (smask >> threadIdx.x & 1)) {
-              double s2 = 0;
-              for (int mm = 0; mm < nmax; ++mm) s2 += coef[mm * 4 + threadIdx.x] * coef[mm * 4 + threadIdx.x];
-              st.csum[threadIdx.x] += s2;
-            }
-            __syncthreads();
-          }
-          for (int i = threadIdx.x; i < 4 * m; i += blockDim.x)
-            if (smask >> (i & 3) & 1) {
-              const T h = (T)SJd[i];
-              Lv[i] = h;
-              Llo[i] = (float)(SJd[i] - (double)h);
-            }
-          __syncthreads();
-        }
+        if (smask && nmax > 0) seam_fp64(SU, U, Ulo, SJd, Lv, Llo, coef, st, m, m_cap, nmax, smask);
       }
       const int amask = st.active[0] | (st.active[1] << 1) | (st.active[2] << 2) | (st.active[3] << 3);
       // S l and H l in one pass (H u_n = H l / beta for an accepted l); in the FP32 form H l as a
@@ -1097,11 +1223,18 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
       if (threadIdx.x < 4) {
         const int c = threadIdx.x;
         st.next_s[c] = 0;
+        st.next_raw[c] = 0;
         if (st.accept[c]) {
+          const int prev = st.src[c];
           st.n[c] += 1;
           st.proj[c] = 1;
           if (st.n[c] >= nu) {
             st.active[c] = 0;
+          } else if (A.mode_b && (prev == SRC_S || prev == SRC_R)) {
+            // the next raw vector: H s_j, formed when s_j was loaded (1), or H applied to the previous
+            // raw vector (2)
+            st.next_raw[c] = prev == SRC_S ? 1 : 2;
+            st.src[c] = SRC_R;
           } else if (st.n[c] == A.p && !st.seam_done[c]) {
             st.next_s[c] = 1;         // the vector after u_p is s_j
             st.seam_done[c] = 1;
@@ -1117,23 +1250,28 @@ __global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) 
       // recomputed here from the stored basis (KV now holds H applied to the dropped s_j)
       const int kmask = (st.act[0] == ACT_LOAD_K) | ((st.act[1] == ACT_LOAD_K) << 1) |
                         ((st.act[2] == ACT_LOAD_K) << 2) | ((st.act[3] == ACT_LOAD_K) << 3);
-      if (kmask) {
-        for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
-          const int r = i >> 2, c = i & 3;
-          if (!(kmask >> c & 1)) continue;
-          const size_t o = (size_t)(st.n[c] - 1) * m_cap * 4 + 4 * r + c;
-          Lv[i] = U[o];
-          if constexpr (sizeof(T) == 4) Llo[i] = Ulo[o];
-        }
-        __syncthreads();
-        if constexpr (sizeof(T) == 4)
-          spmm4_pair<TV>(A.valH, lrow, lcol, rbase, loff, ncl, Lv, Llo, KV, Klo, kmask);
-        else
-          spmm4<TV, T>(A.valH, lrow, lcol, rbase, loff, ncl, Lv, KV, kmask);
-      }
+      if (kmask) reload_hu<TV, T>(A.valH, lrow, lcol, rbase, loff, ncl, m, m_cap, kmask, st, U, Ulo, Lv, Llo, KV, Klo);
+      // reading B: the raw vectors of the s_j chain, each H applied to the one before, scaled by a power
+      // of two near its inverse 2-norm (exact for both halves of a pair). The first, H s_j, is formed when
+      // s_j is loaded as the next vector, from s_j as CG left it (the FP64 seam pass of the FP32 form
+      // orthogonalises its copy of s_j in place); the later ones when the previous raw vector is accepted.
+      int pmask = 0;                         // columns whose next vector is s_j
+      if (A.mode_b)
+        for (int c = 0; c < 4; ++c)
+          pmask |= (st.active[c] && ((st.accept[c] && st.next_s[c]) || st.act[c] == ACT_LOAD_S)) << c;
+      const int rmask = pmask | ((st.next_raw[0] == 2) | ((st.next_raw[1] == 2) << 1) | ((st.next_raw[2] == 2) << 2) |
+                                 ((st.next_raw[3] == 2) << 3));
+      if (rmask)
+        raw_chain_step<TV, T>(A.valH, lrow, lcol, rbase, loff, ncl, m, pmask, rmask, SJ, SJd, RW, RWN, RWlo, RWNlo, red,
+                              sums, scal);
       for (int i = threadIdx.x; i < 4 * m; i += blockDim.x) {
         const int c = i & 3;
         if (!st.active[c]) continue;
+        if (st.next_raw[c]) {
+          Lv[i] = RW[i];
+          if constexpr (sizeof(T) == 4) Llo[i] = RWlo[i];
+          continue;
+        }
         if (st.accept[c]) {
           Lv[i] = st.next_s[c] ? SJ[i] : KV[i];
           if constexpr (sizeof(T) == 4) Llo[i] = st.next_s[c] ? 0.0f : Klo[i];
@@ -1255,12 +1393,14 @@ size_t dyn_smem_bytes(int nu, int clcap, int lnnz_cap, int mcap, size_t elem) {
 
 // Per-CTA global work slot: U and S U ([nu][m_cap][4]) and s_j ([m_cap][4]) in the arithmetic
 // type, then s_j in FP64 ([m_cap][4]), S_r - I of the four columns ([4][nu][nu] FP32), the two
-// streamed work vectors ([m_cap][4] each, arithmetic type), and (FP32 arithmetic) the low half
-// of H u ([m_cap][4]) and of the basis vectors ([nu][m_cap][4]).
+// streamed work vectors ([m_cap][4] each, arithmetic type), (FP32 arithmetic) the low half of H u
+// ([m_cap][4]) and of the basis vectors ([nu][m_cap][4]), then the raw vector of the s_j chain and H
+// applied to it ([m_cap][4] each, arithmetic type) with their FP32 low halves.
 size_t slot_bytes_for(int nu, int mcap, size_t elem) {
   return align_up(elem * ((size_t)2 * nu + 1) * mcap * 4, 256) + align_up(sizeof(double) * 4 * (size_t)mcap, 256) +
          align_up(sizeof(float) * 4 * (size_t)nu * nu, 256) + elem * 2 * (size_t)mcap * 4 +
-         (elem == 4 ? 4 * ((size_t)nu + 1) * mcap * 4 : 0) + 256;
+         align_up(elem == 4 ? sizeof(float) * ((size_t)nu + 1) * mcap * 4 : 0, 256) +
+         (2 * elem + 2 * sizeof(float)) * (size_t)mcap * 4 + 256;
 }
 
 template <typename TV, typename T, int NT>
@@ -1322,6 +1462,13 @@ mka_status launch_t(const mka_system* sys, const AtomsConfig& cf, const AtomsLau
   A.fallback = a.fallback;
   A.cg_only = a.cg_only;
   A.cg_target = a.cg_target;
+  A.mode_b = a.mode_b;
+  A.prev_cl = a.prev_cl;
+  A.prev_s = a.prev_s;
+  A.prev_cap = a.prev_cap;
+  A.keep_cl = a.keep_cl;
+  A.keep_s = a.keep_s;
+  A.keep_cap = a.keep_cap;
   A.red = a.red;
   if (!a.cg_only && !a.red) return fail(MKA_ERR_INVALID_ARG, "the per-atom kernel needs a reduced-problem buffer");
   atoms_kernel<TV, T, NT><<<(unsigned)a.grid, NT, cf.smem, st>>>(A);
@@ -1438,6 +1585,18 @@ mka_status launch_columns(mka_system* sys, mka_result* res, const mka_solve_para
     a.blk_off = res->keep ? res->d_blk_off + off : nullptr;
     a.cv = res->d_cv;
     a.col0 = 4 * off;
+    a.mode_b = prm->subspace == MKA_SUBSPACE_B;
+    if (prm->s_start) {
+      const mka_result* pr = prm->s_start;
+      a.prev_cap = pr->s_cap;
+      a.prev_cl = pr->d_s_cl + off * pr->s_cap;
+      a.prev_s = pr->d_s + 4 * off * 4 * (int64_t)pr->s_cap;
+    }
+    if (res->d_s) {
+      a.keep_cap = res->s_cap;
+      a.keep_cl = res->d_s_cl + off * res->s_cap;
+      a.keep_s = res->d_s + 4 * off * 4 * (int64_t)res->s_cap;
+    }
     a.scratch = scratch;
     a.counter = counter;
     a.red = red;

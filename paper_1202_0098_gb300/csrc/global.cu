@@ -394,7 +394,112 @@ mka_status spmv_dispatch(const mka_system* s, const void* val, int x_dtype, cons
   return spmv_dispatch_k<TV, float>(s, (const TV*)val, x, y, k, st);
 }
 
+// ---- density of states: D(E) = -(1/pi) Im sum_j (G(E + i eta) S)_jj = (eta/pi) sum w / ((E - eps)^2 + eta^2) ----
+// Grid (level chunks, energy tiles of 256): a CTA stages its chunk's levels through shared memory
+// 256 at a time, each thread one energy, and writes its chunk's sum; a second kernel adds the chunk
+// sums in chunk order. FP64 throughout.
+constexpr int kDosThreads = 256;
+constexpr int64_t kDosChunk = 32768;   // levels per CTA
+
+__global__ void __launch_bounds__(kDosThreads) dos_partial_kernel(const double* eps, const double* w, int64_t n,
+                                                                  const double* energies, int n_e, double eta,
+                                                                  double* partial) {
+  __shared__ double se[kDosThreads], sw[kDosThreads];
+  const int64_t l0 = (int64_t)blockIdx.x * kDosChunk, l1 = min(n, l0 + kDosChunk);
+  const int k = blockIdx.y * kDosThreads + threadIdx.x;
+  const double E = k < n_e ? energies[k] : 0.0;
+  const double eta2 = eta * eta;
+  double acc = 0.0;
+  for (int64_t t0 = l0; t0 < l1; t0 += kDosThreads) {
+    const int64_t t = t0 + threadIdx.x;
+    se[threadIdx.x] = t < l1 ? eps[t] : 0.0;
+    sw[threadIdx.x] = t < l1 ? w[t] : 0.0;
+    __syncthreads();
+    const int cnt = (int)(l1 - t0 < kDosThreads ? l1 - t0 : kDosThreads);
+    for (int i = 0; i < cnt; ++i) {
+      const double wi = sw[i];
+      if (wi != 0.0) {
+        const double d = E - se[i];
+        acc += wi / (d * d + eta2);
+      }
+    }
+    __syncthreads();
+  }
+  if (k < n_e) partial[(int64_t)blockIdx.x * n_e + k] = acc;
+}
+
+__global__ void dos_sum_kernel(const double* partial, int64_t n_chunks, int n_e, double scale, double* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_e) return;
+  double s = 0.0;
+  for (int64_t c = 0; c < n_chunks; ++c) s += partial[c * n_e + k];
+  out[k] = scale * s;
+}
+
+// H's on-site blocks += shift[a] on the diagonal (one thread per atom): the diagonal block of row a found in
+// its sorted columns, the stored value decoded, shifted and stored again in its format.
+__global__ void onsite_shift_kernel(const int32_t* row_ptr, const int32_t* col, void* valH, int storage,
+                                    const double* shift, int64_t n) {
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < n; a += (int64_t)gridDim.x * blockDim.x) {
+    int lo = row_ptr[a], hi = row_ptr[a + 1] - 1, k = -1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      if (col[mid] == a) { k = mid; break; }
+      if (col[mid] < a) lo = mid + 1; else hi = mid - 1;
+    }
+    if (k < 0) continue;
+    for (int o = 0; o < 4; ++o) {
+      const int64_t i = (int64_t)k * 16 + 5 * o;
+      if (storage == MKA_FP64) reinterpret_cast<double*>(valH)[i] += shift[a];
+      else if (storage == MKA_MIXED_FP32) reinterpret_cast<float*>(valH)[i] = (float)((double)reinterpret_cast<float*>(valH)[i] + shift[a]);
+      else {
+        __nv_bfloat16* v = reinterpret_cast<__nv_bfloat16*>(valH);
+        v[i] = __double2bfloat16((double)__bfloat162float(v[i]) + shift[a]);
+      }
+    }
+  }
+}
+
 }  // namespace
+
+mka_status launch_onsite_shift(mka_system* sys, const double* shift_host, cudaStream_t st) {
+  double* d = nullptr;
+  MKA_CUDA_TRY(cudaMallocAsync(&d, sizeof(double) * sys->n_atoms, st));
+  cudaError_t e = cudaMemcpyAsync(d, shift_host, sizeof(double) * sys->n_atoms, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((sys->n_atoms + 255) / 256, 4096));
+    onsite_shift_kernel<<<(unsigned)blocks, 256, 0, st>>>(sys->d_row_ptr, sys->d_col, sys->d_valH, sys->storage, d,
+                                                         sys->n_atoms);
+    count_launches();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(d, st);
+  if (e != cudaSuccess) return cuda_fail(e, "mka_system_shift_onsite");
+  return MKA_OK;
+}
+
+mka_status launch_dos(const double* eps, const double* w, int64_t n, const double* energies, int n_e, double eta,
+                      cudaStream_t st, double* dos_host) {
+  const int64_t n_chunks = std::max<int64_t>(1, (n + kDosChunk - 1) / kDosChunk);
+  double* buf = nullptr;
+  MKA_CUDA_TRY(cudaMallocAsync(&buf, sizeof(double) * ((size_t)n_chunks * n_e + 2 * (size_t)n_e), st));
+  double* d_e = buf + (size_t)n_chunks * n_e;
+  double* d_out = d_e + n_e;
+  cudaError_t e = cudaMemcpyAsync(d_e, energies, sizeof(double) * n_e, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) {
+    const dim3 grid((unsigned)n_chunks, (unsigned)((n_e + kDosThreads - 1) / kDosThreads));
+    dos_partial_kernel<<<grid, kDosThreads, 0, st>>>(eps, w, n, d_e, n_e, eta, buf);
+    dos_sum_kernel<<<(n_e + 255) / 256, 256, 0, st>>>(buf, n_chunks, n_e, eta / 3.14159265358979323846, d_out);
+    count_launches(2);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dos_host, d_out, sizeof(double) * n_e, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(buf, st);
+  if (e != cudaSuccess) return cuda_fail(e, "mka_dos");
+  return MKA_OK;
+}
 
 size_t mu_buffer_bytes() { return sizeof(MuState) + sizeof(double) * 2 * kMaxRedBlocks + 64; }
 

@@ -79,6 +79,9 @@ struct mka_result {
   double* d_cv = nullptr;         // kept C and V_j, lane-interleaved [n_cols / 32][kept_block_doubles][32]
   double* d_mu_state = nullptr;   // bisection bracket and partial sums
   int32_t* d_fallback = nullptr;  // [n_cols] warm-start fallback flags (learned start only)
+  int s_cap = 0;                  // kept s_j: atoms per cluster slot (0: not kept)
+  int32_t* d_s_cl = nullptr;      // [n_sel][s_cap] cluster atom ids, ascending, -1 beyond the count
+  double* d_s = nullptr;          // [n_cols][4 s_cap] s_j on those atoms' orbitals
   std::vector<int64_t> h_sel;
   std::vector<int64_t> h_blk_off;
 };
@@ -120,6 +123,13 @@ struct AtomsLaunchArgs {
   const int32_t* patch = nullptr;  // [n_sel][17]
   int32_t* fallback = nullptr;     // [4 n_sel] or NULL
   int cg_only = 0;                 // 1: stop after CG, write s_j on the patch into cg_target
+  int mode_b = 0;                  // 1: the literal direct sum K_p(H; e_j) + K_q(H; s_j)
+  const int32_t* prev_cl = nullptr;  // earlier s_j as the CG start (see the kernel's Args)
+  const double* prev_s = nullptr;
+  int prev_cap = 0;
+  int32_t* keep_cl = nullptr;        // keep this solve's s_j
+  double* keep_s = nullptr;
+  int keep_cap = 0;
   float* cg_target = nullptr;      // [4 n_sel][68]
   // reduced problems of the selection, lane-interleaved: [ceil(4 n_sel / 32)][red_block_doubles(nu)][32]
   // (not used with cg_only)
@@ -173,6 +183,9 @@ mka_status launch_density(mka_system* sys, mka_result* res, double mu, double kT
 mka_status launch_greens(mka_system* sys, mka_result* res, double z_re, double z_im, double* g_out);
 mka_status launch_spmv(const mka_system* sys, int which, int x_dtype, const void* x, void* y, int k,
                        cudaStream_t st);
+mka_status launch_onsite_shift(mka_system* sys, const double* shift_host, cudaStream_t st);
+mka_status launch_dos(const double* eps, const double* w, int64_t n, const double* energies, int n_e, double eta,
+                      cudaStream_t st, double* dos_host);
 
 // Stream-ordered (no host synchronisation, no allocation) variants used by plans and graphs.
 size_t mu_buffer_bytes();

@@ -203,6 +203,7 @@ mka_status plan_enqueue(mka_plan* P, int64_t n, const PlanMode& m) {
   a.red = P->red;
   a.cv = r->d_cv;
   a.col0 = 0;
+  a.mode_b = P->prm.subspace == MKA_SUBSPACE_B;
   a.grid = (int)std::min<int64_t>(n, P->grid);
   MKA_CUDA_TRY(cudaEventRecordWithFlags(P->k0, st, cudaEventRecordExternal));
   mka_status s = atoms_launch(P->sys, P->prm.arith, P->cf, a, st);
@@ -260,6 +261,9 @@ mka_status mka_plan_create(mka_system* sys, int64_t max_atoms, const mka_solve_p
   if (prm->arith != MKA_FP64 && prm->arith != MKA_MIXED_FP32)
     return fail(MKA_ERR_INVALID_ARG, "arith must be MKA_FP64 or MKA_MIXED_FP32");
   if (!(prm->cg_tol > 0) || prm->cg_maxit < 1) return fail(MKA_ERR_INVALID_ARG, "need cg_tol > 0, cg_maxit >= 1");
+  if (prm->subspace != MKA_SUBSPACE_A && prm->subspace != MKA_SUBSPACE_B)
+    return fail(MKA_ERR_INVALID_ARG, "subspace must be MKA_SUBSPACE_A or MKA_SUBSPACE_B");
+  if (prm->s_start || prm->keep_s) return fail(MKA_ERR_INVALID_ARG, "keep_s and s_start are for direct solves");
   if (prm->use_warm_start && !sys->warm)
     return fail(MKA_ERR_INVALID_ARG, "use_warm_start needs a network attached with mka_system_set_warm_start");
   mka_tuning t{256, 0, 0};
@@ -437,6 +441,7 @@ mka_status mka_autotune(mka_system* sys, const mka_solve_params* prm, const int6
   const int max_cl = *std::max_element(sz.begin(), sz.end());
   std::ostringstream key;
   key << prop.name << "|storage=" << sys->storage << "|arith=" << prm->arith << "|nu=" << prm->p + prm->q
+      << "|subspace=" << prm->subspace
       << "|maxcl=" << (max_cl / 16) * 16 << "|nsample=" << n_sample;
   const std::string k = key.str();
   std::vector<std::string> lines;
@@ -504,6 +509,89 @@ mka_status mka_autotune(mka_system* sys, const mka_solve_params* prm, const int6
     }
     f << "{\"key\": \"" << k << "\", \"threads\": " << best_t.threads << ", \"ctas_per_sm\": " << best_t.ctas_per_sm
       << ", \"order_by_size\": " << best_t.order_by_size << ", \"ms\": " << best / 2.0 << "}\n]}\n";
+  }
+  return MKA_OK;
+}
+
+mka_status mka_autotune_batch(mka_system* sys, const mka_solve_params* prm, const mka_tuning* tune,
+                              const int64_t* candidates, int n_candidates, int64_t first_atom,
+                              double electrons_per_atom, double kT, const char* cache_path, void* stream,
+                              int64_t* out_batch) {
+  if (!sys || !prm || !candidates || n_candidates < 1 || !out_batch || first_atom < 0 || first_atom >= sys->n_atoms)
+    return fail(MKA_ERR_INVALID_ARG, "bad batch-autotune arguments");
+  for (int i = 0; i < n_candidates; ++i)
+    if (candidates[i] < 1 || candidates[i] > sys->n_atoms) return fail(MKA_ERR_INVALID_ARG, "candidate batch out of range");
+  mka_tuning t = tune ? *tune : mka_tuning{256, 0, 0};
+  int dev = 0;
+  cudaDeviceProp prop{};
+  MKA_CUDA_TRY(cudaGetDevice(&dev));
+  MKA_CUDA_TRY(cudaGetDeviceProperties(&prop, dev));
+  std::ostringstream key;
+  key << prop.name << "|storage=" << sys->storage << "|arith=" << prm->arith << "|nu=" << prm->p + prm->q
+      << "|subspace=" << prm->subspace << "|atoms=" << sys->n_atoms << "|threads=" << t.threads
+      << "|ctas=" << t.ctas_per_sm << "|order=" << t.order_by_size << "|batch_of";
+  for (int i = 0; i < n_candidates; ++i) key << ":" << candidates[i];
+  const std::string k = key.str();
+  std::vector<std::string> lines;
+  if (cache_path) {
+    std::ifstream f(cache_path);
+    std::string line;
+    while (std::getline(f, line)) {
+      if (line.find("\"key\"") == std::string::npos) continue;
+      lines.push_back(line);
+      if (line.find("\"key\": \"" + k + "\"") != std::string::npos) {
+        long long b = 0;
+        const size_t pos = line.find("\"batch\"");
+        if (pos != std::string::npos && sscanf(line.c_str() + pos, "\"batch\": %lld", &b) == 1 && b > 0) {
+          *out_batch = b;
+          return MKA_OK;
+        }
+      }
+    }
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  MKA_CUDA_TRY(cudaEventCreate(&e0));
+  MKA_CUDA_TRY(cudaEventCreate(&e1));
+  double best = -1.0;
+  int64_t best_b = candidates[0];
+  std::vector<int64_t> atoms;
+  for (int i = 0; i < n_candidates; ++i) {
+    const int64_t B = candidates[i];
+    atoms.resize(B);
+    for (int64_t a = 0; a < B; ++a) atoms[a] = (first_atom + a) % sys->n_atoms;
+    mka_plan* P = nullptr;
+    if (mka_plan_create(sys, B, prm, &t, stream, &P) != MKA_OK) continue;   // does not fit
+    bool ok = mka_plan_run(P, atoms.data(), B, electrons_per_atom * B, kT, nullptr) == MKA_OK;   // capture + warm
+    float ms = 0;
+    if (ok) {
+      cudaEventRecord(e0, st);
+      ok = mka_plan_run(P, atoms.data(), B, electrons_per_atom * B, kT, nullptr) == MKA_OK;
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    mka_plan_destroy(P);
+    const double rate = ok && ms > 0 ? 4.0 * B / (ms / 1e3) : -1.0;
+    if (rate > best) {
+      best = rate;
+      best_b = B;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0) return fail(MKA_ERR_OOM, "no candidate batch size fits");
+  *out_batch = best_b;
+  if (cache_path) {
+    std::ofstream f(cache_path, std::ios::trunc);
+    f << "{\"entries\": [\n";
+    for (auto& l : lines) {
+      if (l.find("\"key\": \"" + k + "\"") != std::string::npos) continue;
+      std::string x = l;
+      while (!x.empty() && (x.back() == ',' || x.back() == ' ')) x.pop_back();
+      f << x << ",\n";
+    }
+    f << "{\"key\": \"" << k << "\", \"batch\": " << best_b << ", \"columns_per_s\": " << best << "}\n]}\n";
   }
   return MKA_OK;
 }

@@ -27,6 +27,7 @@ namespace mka {
 namespace {
 
 enum : int { RS_OK = 0, RS_NOT_SPD = MKA_ERR_NOT_SPD, RS_BREAKDOWN = MKA_ERR_BREAKDOWN };
+constexpr int kSmallNu = 64;
 
 struct RedArgs {
   double* blk;               // [groups][red_block_doubles(nu)][32], in place
@@ -229,13 +230,16 @@ __device__ bool lane_tql(const Lane& M, int n, double* d, double* e, double* rc,
   return true;
 }
 
+// NUCAP bounds nu: the lane's vectors live in local memory sized NUCAP, so subspaces up to 64 take
+// the small instance and larger ones (up to MKA_MAX_NU) the large one.
+template <int NUCAP>
 __global__ void __launch_bounds__(128) reduced_kernel(const RedArgs A) {
   const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= A.n_cols) return;
   const int nu = A.nu;
   const Lane M{A.blk + (size_t)(col >> 5) * red_block_doubles(nu) * 32 + (col & 31), nu};
-  double d[MKA_MAX_NU], e[MKA_MAX_NU], rdiag[MKA_MAX_NU], p[MKA_MAX_NU], tau[MKA_MAX_NU], v[MKA_MAX_NU];
-  int rank[MKA_MAX_NU];
+  double d[NUCAP], e[NUCAP], rdiag[NUCAP], p[NUCAP], tau[NUCAP], v[NUCAP];
+  int rank[NUCAP];
   const int n = A.nu_eff[col];
   const int st_in = A.status[col];
   bool ok = st_in == RS_OK && n > 0 && n <= nu;
@@ -317,7 +321,9 @@ mka_status reduced_launch(double* blk, int64_t n_cols, int nu, int32_t* status, 
   A.cv = cv;
   A.col0 = col0;
   const int threads = 128;
-  reduced_kernel<<<(unsigned)((n_cols + threads - 1) / threads), threads, 0, st>>>(A);
+  const unsigned blocks = (unsigned)((n_cols + threads - 1) / threads);
+  if (nu <= kSmallNu) reduced_kernel<kSmallNu><<<blocks, threads, 0, st>>>(A);
+  else reduced_kernel<MKA_MAX_NU><<<blocks, threads, 0, st>>>(A);
   count_launches();
   MKA_CUDA_TRY(cudaGetLastError());
   return MKA_OK;

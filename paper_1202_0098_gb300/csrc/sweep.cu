@@ -80,7 +80,7 @@ struct PackArgs {
   int64_t a0, blk0;
   double* g_eps;
   double* g_w;
-  uint8_t* g_win;
+  uint16_t* g_win;
   uint8_t* g_flag;
   double* g_occ;
   double* g_part;
@@ -146,8 +146,8 @@ __global__ void __launch_bounds__(128) sweep_pack_kernel(const PackArgs A) {
           a < cnt ? b[(size_t)(n * nu + lo + a) * 32] * b[(size_t)(nu * nu + lo + a) * 32] : 0.0;
   }
   if (threadIdx.x < 4) {
-    A.g_win[2 * (4 * la + threadIdx.x)] = (uint8_t)s_lo[threadIdx.x];
-    A.g_win[2 * (4 * la + threadIdx.x) + 1] = (uint8_t)s_cnt[threadIdx.x];
+    A.g_win[2 * (4 * la + threadIdx.x)] = (uint16_t)s_lo[threadIdx.x];
+    A.g_win[2 * (4 * la + threadIdx.x) + 1] = (uint16_t)s_cnt[threadIdx.x];
   }
   __syncthreads();
   const int nrow = A.row_ptr[atom + 1] - A.row_ptr[atom];
@@ -286,7 +286,7 @@ __global__ void sweep_bisect_step_kernel(const double* count, int64_t n_chunks, 
 
 struct RhoArgs {
   const double* eps;
-  const uint8_t* win;
+  const uint16_t* win;
   const uint8_t* flag;
   const double* occ;
   const double* part;
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(256) sweep_rho_kernel(const RhoArgs A) {
     if (A.flag[la] != 1) continue;     // overflowed: solved again instead
     for (int i = lane; i < 4 * kp; i += 32) {
       const int c = i / kp, a = i % kp;
-      const uint8_t* wn = A.win + 2 * (4 * la + c);
+      const uint16_t* wn = A.win + 2 * (4 * la + c);
       f[i] = a < wn[1] ? fermi_f(A.eps[(4 * la + c) * nu + wn[0] + a], A.mu, A.kT) : 0.0;
     }
     __syncwarp();
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(256) sweep_rho_kernel(const RhoArgs A) {
 // xor tree into g[block] (3 doubles).
 struct ForceArgs {
   const double* eps;
-  const uint8_t* win;
+  const uint16_t* win;
   const uint8_t* flag;
   const double* occ;
   const double* occ_pi;
@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(256) sweep_force_kernel(const ForceArgs A) {
     if (A.flag[la] != 1) continue;
     for (int i = lane; i < 4 * kp; i += 32) {
       const int c = i / kp, a = i % kp;
-      const uint8_t* wn = A.win + 2 * (4 * la + c);
+      const uint16_t* wn = A.win + 2 * (4 * la + c);
       const double x = a < wn[1] ? A.eps[(4 * la + c) * nu + wn[0] + a] : 0.0;
       const double fx = a < wn[1] ? fermi_f(x, A.mu, A.kT) : 0.0;
       f[i] = fx;
@@ -433,7 +433,7 @@ struct mka_sweep {
   int64_t chunk_atoms = 0, chunk0 = 0, n_chunks = 0;
   double* d_eps = nullptr;              // [4 n][nu]
   double* d_w = nullptr;
-  uint8_t* d_win = nullptr;             // [4 n][2]: first window level, count
+  uint16_t* d_win = nullptr;            // [4 n][2]: first window level, count
   uint8_t* d_flag = nullptr;            // [n]: 1 stored, 3 stored and overflowed
   double* d_occ = nullptr;              // [nblk][16]
   double* d_part = nullptr;             // [nblk][16][kp]
@@ -582,6 +582,8 @@ mka_status mka_sweep_create(mka_system* sys, int64_t atom_begin, int64_t atom_en
     return fail(MKA_ERR_INVALID_ARG, "need 0 <= atom_begin < atom_end <= n_atoms");
   if (nu < 1 || nu > MKA_MAX_NU) return fail(MKA_ERR_INVALID_ARG, "need 1 <= nu <= MKA_MAX_NU");
   if (kp < 1 || kp > nu) return fail(MKA_ERR_INVALID_ARG, "need 1 <= kp <= nu");
+  if (pack_smem_bytes(nu, kp) > (size_t)200 * 1024)
+    return fail(MKA_ERR_INVALID_ARG, "kp too large for nu: the packing kernel holds 32 nu (kp + 2) bytes in shared memory");
   if (!(win_lo < win_hi)) return fail(MKA_ERR_INVALID_ARG, "need win_lo < win_hi");
   if (chunk_atoms < 1) return fail(MKA_ERR_INVALID_ARG, "need chunk_atoms >= 1");
   if (with_forces && !sys->have_sk) return fail(MKA_ERR_INVALID_ARG, "forces need the Slater-Koster model (mka_build_system)");
@@ -610,7 +612,7 @@ mka_status mka_sweep_create(mka_system* sys, int64_t atom_begin, int64_t atom_en
   }
   ALLOC(sw->d_eps, sizeof(double) * 4 * n * nu);
   ALLOC(sw->d_w, sizeof(double) * 4 * n * nu);
-  ALLOC(sw->d_win, 2 * 4 * n);
+  ALLOC(sw->d_win, sizeof(uint16_t) * 2 * 4 * n);
   ALLOC(sw->d_flag, n);
   ALLOC(sw->d_occ, sizeof(double) * 16 * sw->nblk);
   ALLOC(sw->d_part, sizeof(double) * 16 * sw->nblk * kp);

@@ -21,7 +21,7 @@ MKA_ERR_OOM, MKA_ERR_CUDA, MKA_ERR_TIMEOUT, MKA_ERR_CLUSTER_TOO_LARGE = 5, 6, 7,
 MKA_FP64, MKA_MIXED_FP32, MKA_MIXED_BF16 = 0, 1, 2
 STORAGE = {"fp64": MKA_FP64, "fp32": MKA_MIXED_FP32, "bf16": MKA_MIXED_BF16}
 MKA_MAX_CLUSTER_ATOMS = 512
-MKA_MAX_NU = 64
+MKA_MAX_NU = 320
 MKA_STATIC_SCRATCH_BYTES = 64 << 20
 
 # Every symbol include/mka.h declares (checked by the tests).
@@ -35,7 +35,7 @@ EXPORTED = [
     "mka_cg_patch_targets", "mka_system_set_warm_start", "mka_result_copy_warm_start",
     "mka_sweep_create", "mka_sweep_info", "mka_plan_run_sweep", "mka_sweep_status", "mka_sweep_level_range",
     "mka_sweep_find_mu", "mka_sweep_density", "mka_sweep_forces", "mka_sweep_chunk_sums", "mka_sweep_device_levels",
-    "mka_sweep_destroy", "mka_forces",
+    "mka_sweep_destroy", "mka_forces", "mka_dos", "mka_system_shift_onsite", "mka_autotune_batch",
     "mka_kernel_launches", "mka_last_error", "mka_status_string",
 ]
 
@@ -57,7 +57,8 @@ class mka_tuning(C.Structure):
 
 class mka_solve_params(C.Structure):
     _fields_ = [("p", C.c_int), ("q", C.c_int), ("arith", C.c_int), ("use_warm_start", C.c_int),
-                ("cg_tol", C.c_double), ("cg_maxit", C.c_int), ("keep_vectors", C.c_int)]
+                ("cg_tol", C.c_double), ("cg_maxit", C.c_int), ("keep_vectors", C.c_int), ("keep_s", C.c_int),
+                ("s_start", C.c_void_p), ("subspace", C.c_int)]
 
 
 _lib = None
@@ -112,6 +113,9 @@ def load(path: str | None = None) -> C.CDLL:
         "mka_sweep_create": [P, I64, I64, I32, D, D, I32, I64, I32, P, P],
         "mka_sweep_forces": [P, P, D, D, P, P],
         "mka_forces": [P, P, D, D, P, P],
+        "mka_dos": [P, P, I64, P, I32, D, P, P],
+        "mka_system_shift_onsite": [P, P, P],
+        "mka_autotune_batch": [P, P, P, P, I32, I64, D, D, C.c_char_p, P, P],
         "mka_sweep_info": [P, P, P, P, P],
         "mka_plan_run_sweep": [P, P, P, I64],
         "mka_sweep_status": [P, P, P],
@@ -232,8 +236,12 @@ def mka_spmv(sys, which: int, x_dtype: int, x_ptr: int, y_ptr: int, k: int = 1, 
 
 
 def solve_params(p: int, q: int, arith: str = "fp64", cg_tol: float = 1e-12, cg_maxit: int = 500,
-                 keep_vectors: bool = True, use_warm_start: bool = False) -> mka_solve_params:
+                 keep_vectors: bool = True, use_warm_start: bool = False, subspace: str = "A", keep_s: bool = False,
+                 s_start=None) -> mka_solve_params:
     prm = mka_solve_params()
+    prm.subspace = {"A": 0, "B": 1}[subspace]
+    prm.keep_s = int(keep_s)
+    prm.s_start = s_start.value if isinstance(s_start, C.c_void_p) else s_start
     prm.p, prm.q = p, q
     prm.arith = MKA_FP64 if arith == "fp64" else MKA_MIXED_FP32
     prm.use_warm_start = int(use_warm_start)
@@ -311,6 +319,20 @@ def mka_greens(sys, res, z: complex, g_ptr: int):
     _check(load().mka_greens(sys, res, float(z.real), float(z.imag), C.c_void_p(g_ptr)), "mka_greens")
 
 
+def mka_system_shift_onsite(sys, shift: np.ndarray, stream: int = 0):
+    a = np.ascontiguousarray(shift, dtype=np.float64)
+    _check(load().mka_system_shift_onsite(sys, _ptr(a), C.c_void_p(stream)), "mka_system_shift_onsite")
+
+
+def mka_dos(eps_ptr: int, w_ptr: int, n_levels: int, energies, eta: float, stream: int = 0) -> np.ndarray:
+    """Density of states at `energies` from levels and weights in device memory (see include/mka.h)."""
+    e = np.ascontiguousarray(energies, dtype=np.float64)
+    out = np.empty(e.shape[0])
+    _check(load().mka_dos(C.c_void_p(eps_ptr), C.c_void_p(w_ptr), int(n_levels), _ptr(e), e.shape[0], float(eta),
+                          C.c_void_p(stream), _ptr(out)), "mka_dos")
+    return out
+
+
 def tuning(threads: int = 256, ctas_per_sm: int = 0, order_by_size: bool = False) -> mka_tuning:
     t = mka_tuning()
     t.threads, t.ctas_per_sm, t.order_by_size = threads, ctas_per_sm, int(order_by_size)
@@ -370,6 +392,17 @@ def mka_autotune(sys, prm: mka_solve_params, sample: np.ndarray, n_electrons: fl
                                cache_path.encode() if cache_path else None, C.c_void_p(stream), C.byref(out)),
            "mka_autotune")
     return out
+
+
+def mka_autotune_batch(sys, prm: mka_solve_params, tune: mka_tuning | None, candidates, first_atom: int,
+                       electrons_per_atom: float, kT: float, cache_path: str | None = None, stream: int = 0) -> int:
+    c = np.ascontiguousarray(candidates, dtype=np.int64)
+    out = C.c_int64()
+    _check(load().mka_autotune_batch(sys, C.byref(prm), C.byref(tune) if tune is not None else None, _ptr(c),
+                                     c.shape[0], int(first_atom), float(electrons_per_atom), float(kT),
+                                     cache_path.encode() if cache_path else None, C.c_void_p(stream), C.byref(out)),
+           "mka_autotune_batch")
+    return out.value
 
 
 # ---- whole-system sweep ------------------------------------------------------------------

@@ -1,6 +1,8 @@
 """Edge cases of the CUDA path through the C ABI, against the FP64 oracle.
 
-* the largest subspace the library accepts (nu = MKA_MAX_NU = 64, p = q = 32);
+* the largest subspace of each instance of the reduced kernel (nu = 64, p = q = 32) and the
+  largest the library accepts (nu = MKA_MAX_NU = 320, p = q = 160, on the 512-atom system whose
+  clusters, m_c about 636, are larger than nu);
 * an atom listed twice in one selection (its columns are independent of the rest, so both
   copies equal each other and the oracle);
 * a cluster larger than the declared cap (the allocation-free entry point with
@@ -51,12 +53,21 @@ def density(mka, s, res, mu, kT):
     return rho.cpu().numpy().reshape(nb, 4, 4), e
 
 
-def test_largest_subspace(lib, system):
+@pytest.mark.parametrize("half", [32, 160])
+def test_largest_subspace(lib, system, half):
     mka = lib
-    pos, box, s = system
+    if half == 32:
+        pos, box, s = system
+        R = 5.0
+    else:
+        from synth import WORKLOADS, workload_positions
+        pos, box = workload_positions(WORKLOADS["diamond512"])
+        R = 6.0
+        s = mka.mka_build_system(pos, box, SK_CARBON_LIKE, "fp64", cluster_radius=R)
     atoms = np.array([3, 77, 150], dtype=np.int64)
-    p = q = mka.MKA_MAX_NU // 2
-    ores = solve_atoms_parallel(pos, box, SK_CARBON_LIKE, 5.0, atoms, p, q)
+    p = q = half
+    assert 2 * half <= mka.MKA_MAX_NU
+    ores = solve_atoms_parallel(pos, box, SK_CARBON_LIKE, R, atoms, p, q)
     res, lv = solve(mka, s, atoms, p, q)
     try:
         oe, ow = osys.stack_eps_w(ores)
@@ -69,6 +80,8 @@ def test_largest_subspace(lib, system):
         assert abs(e - oe_band) / len(atoms) < TOL
     finally:
         mka.mka_result_destroy(res)
+        if half != 32:
+            mka.mka_system_destroy(s)
 
 
 def test_repeated_atom(lib, system):

@@ -108,3 +108,15 @@ def test_autotune_picks_a_shape_and_caches_it(setup, tmp_path):
     assert len(entries) == 1 and entries[0]["threads"] == t1.threads and entries[0]["ms"] > 0
     t2 = mka.mka_autotune(s, prm, sample, 4.0 * 64, w.kT, cache)     # from the cache
     assert (t2.threads, t2.ctas_per_sm, t2.order_by_size) == (t1.threads, t1.ctas_per_sm, t1.order_by_size)
+
+
+def test_autotune_batch_picks_a_candidate_and_caches_it(setup, tmp_path):
+    mka, w, s = setup
+    prm = mka.solve_params(w.p, w.q, arith="mixed", cg_tol=1e-7, keep_vectors=True)
+    cache = str(tmp_path / "tune.json")
+    cands = [32, 128, 512]
+    b = mka.mka_autotune_batch(s, prm, mka.tuning(), cands, 0, w.electrons_per_atom, w.kT, cache)
+    assert b in cands
+    entry = [e for e in json.load(open(cache))["entries"] if "batch_of" in e["key"]]
+    assert len(entry) == 1 and entry[0]["batch"] == b and entry[0]["columns_per_s"] > 0
+    assert mka.mka_autotune_batch(s, prm, mka.tuning(), cands, 0, w.electrons_per_atom, w.kT, cache) == b

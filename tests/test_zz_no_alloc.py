@@ -146,7 +146,7 @@ def test_static_scratch_rejects_bad_requests_on_the_host(lib):
     s = mka.mka_build_system(pos, box, SK_CARBON_LIKE, "fp64", cluster_radius=5.0)
     try:
         atoms = np.array([0], dtype=np.int64)
-        for p, q, max_cl in ((40, 25, 64), (8, 8, mka.MKA_MAX_CLUSTER_ATOMS + 1), (0, 8, 64)):
+        for p, q, max_cl in ((200, mka.MKA_MAX_NU - 199, 64), (8, 8, mka.MKA_MAX_CLUSTER_ATOMS + 1), (0, 8, 64)):
             n, nu = 4 * len(atoms), max(1, p + q)
             buf = torch.empty(n * nu, dtype=torch.float64, device="cuda")
             buf2 = torch.empty(n * nu, dtype=torch.float64, device="cuda")
