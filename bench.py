@@ -183,6 +183,14 @@ def column_flops(m, nnz, nu, cg_it, n_pattern_rows):
     return spmv + cg_vec + gs + norms + proj + red + out
 
 
+def oracle_pool(mp, cores):
+    """A spawn pool of `cores` oracle processes, each with one BLAS thread (the children inherit the
+    environment), so the host runs one thread per core."""
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    return mp.get_context("spawn").Pool(cores)
+
+
 def run_reference(args, rank, world):
     """The oracle on the host cores, a bounded sample of the same workload per step."""
     import multiprocessing as mp
@@ -193,10 +201,9 @@ def run_reference(args, rank, world):
     cores = os.cpu_count() or 1
     per_step = max(cores, 16)
     from oracle.parallel import _work
-    ctx = mp.get_context("spawn")
     rng = np.random.default_rng(0)
     times = []
-    with ctx.Pool(cores) as pool:
+    with oracle_pool(mp, cores) as pool:
         for it in range(args.warmup + args.steps):
             atoms = np.sort(rng.choice(pos.shape[0], per_step, replace=False))
             chunks = [atoms[i::cores] for i in range(cores)]
@@ -225,8 +232,7 @@ def cpu_baseline(w, pos, box, budget_s=20.0):
     from oracle.parallel import _work
     cores = os.cpu_count() or 1
     rng = np.random.default_rng(1)
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(cores) as pool:
+    with oracle_pool(mp, cores) as pool:
         pool.map(_work, [(pos, box, w.sk, w.R, [0], 2, 1, "fp64", 1e-13)] * cores)   # warm the workers
         n_at = cores
         atoms = np.sort(rng.choice(pos.shape[0], n_at, replace=False))
@@ -243,7 +249,7 @@ def cpu_baseline(w, pos, box, budget_s=20.0):
             n_at += n_more
     return {"value": 4 * n_at / dt, "unit": "columns/s", "cores": cores, "kind": "oracle",
             "sample": f"{n_at} random atoms ({4 * n_at} columns) of {w.name}, FP64 numpy oracle, "
-                      f"one spawn process per core"}
+                      f"one spawn process per core, one BLAS thread each"}
 
 
 def flops_split(m, nnz, nu, cg_it, n_pattern_rows):
@@ -297,7 +303,7 @@ def train_warm_start(mka, torch, seed=100):
         pos, box = lattice_positions(lat, a, nc, sig, vac, seed + k)
         s = mka.mka_build_system(pos, box, skp, "bf16", cluster_radius=R)
         atoms = np.sort(np.random.default_rng(seed + k).choice(pos.shape[0], 12500, replace=False)).astype(np.int64)
-        X, Y, _ = warm_start.collect(s, atoms, "mixed", 1e-7)
+        X, Y, _ = warm_start.collect(s, atoms, "fp64", 1e-12)
         Xs.append(X)
         Ys.append(Y)
         mka.mka_system_destroy(s)
@@ -306,10 +312,45 @@ def train_warm_start(mka, torch, seed=100):
     mse0 = warm_start.mse(net, X, Y)
     hist = warm_start.train(net, X, Y, epochs=20, batch=1024, lr=1e-3, seed=seed)
     info = {"samples": int(X.shape[0]), "generators": "fcc (config-2) and diamond sigma 0.15 (config-3), seeds "
-            f"{seed}-{seed + 3}", "epochs": 20, "batch": 1024, "mse_init": mse0, "mse_final": hist[-1],
-            "train_s": time.perf_counter() - t0}
+            f"{seed}-{seed + 3}", "targets": "inner CG, FP64 form, tolerance 1e-12", "epochs": 20, "batch": 1024,
+            "mse_init": mse0, "mse_final": hist[-1], "train_s": time.perf_counter() - t0}
     del X, Y, Xs, Ys
     return net, info
+
+
+def learned_eval(mka, torch, net, n_atoms=8192, seed=4):
+    """The learned start on a fresh seed of the 10^6-atom amorphous-like generator (50^3 diamond cells,
+    sigma 0.15, R = 7 A, p = q = 20, BF16 values, mixed form): CG iterations with and without it, the fallback
+    rate, and the change of rho and of the band energy at the plain solve's mu."""
+    from synth import SK_CARBON_LIKE, lattice_positions
+    pos, box = lattice_positions("diamond", 3.567, 50, 0.15, 0.0, seed)
+    s = mka.mka_build_system(pos, box, SK_CARBON_LIKE, "bf16", cluster_radius=7.0)
+    mka.mka_system_set_warm_start(s, net)
+    atoms = np.sort(np.random.default_rng(seed).choice(pos.shape[0], n_atoms, replace=False)).astype(np.int64)
+    out = {}
+    for learned in (False, True):
+        prm = mka.solve_params(20, 20, arith="mixed", cg_tol=1e-7, keep_vectors=True, use_warm_start=learned)
+        res = mka.mka_solve_columns(s, atoms, prm)
+        lv = mka.mka_result_copy_levels(res, check=False)
+        out[learned] = (res, lv)
+    mu = mka.mka_find_mu(out[False][0], 4.0 * n_atoms, 0.1)
+    rho, e = {}, {}
+    for learned in (False, True):
+        res = out[learned][0]
+        r = torch.empty(mka.mka_result_info(res)["n_blocks"] * 16, dtype=torch.float64, device="cuda")
+        e[learned], _ = mka.mka_density_energy(s, res, mu, 0.1, r.data_ptr())
+        rho[learned] = r
+    rec = {"system": f"diamond 50^3 cells, sigma 0.15, seed {seed} (unseen in training), {n_atoms} random atoms",
+           "cg_iters_plain": float(out[False][1]["cg_iters"].mean()),
+           "cg_iters_learned": float(out[True][1]["cg_iters"].mean()),
+           "fallback_rate": float(mka.mka_result_copy_warm_start(out[True][0]).mean()),
+           "max_abs_drho": float((rho[True] - rho[False]).abs().max().item()),
+           "abs_dE_eV_per_atom": abs(e[True] - e[False]) / n_atoms}
+    rec["iterations_saved"] = 1.0 - rec["cg_iters_learned"] / rec["cg_iters_plain"]
+    for learned in out:
+        mka.mka_result_destroy(out[learned][0])
+    mka.mka_system_destroy(s)
+    return rec
 
 
 def run_form(mka, torch, sysh, w, form, B, batch_atoms, steps, warmup, stream, tune_cache, rank, autotune=True,
@@ -430,9 +471,10 @@ def sample_window(mka, plan, atoms, w, half):
     return mu_s, (lo, hi), int(cnt.max())
 
 
-def sweep_flow(mka, torch, D, sysh, plan, sw, slices, B, w, n_total, n_chunks, rho, stream, group, kms):
-    """The whole work flow over the rank's slices: plan batches into the sweep, then the global mu, rho and
-    energies. Per-batch kernel times are appended to kms. Returns the global scalars."""
+def sweep_flow(mka, torch, D, sysh, plan, sw, slices, B, w, n_total, n_chunks, rho, stream, group, kms, F=None):
+    """The whole work flow of Eq. EQ-WORK-FLOW over the rank's slices: plan batches into the sweep, then the
+    global mu, rho, the energies and (F given) the forces. Per-batch kernel times are appended to kms.
+    Returns the global scalars."""
     for sl in slices:
         for b in batches_of(sl, B):
             mka.mka_plan_run_sweep(plan, sw, b)
@@ -444,7 +486,10 @@ def sweep_flow(mka, torch, D, sysh, plan, sw, slices, B, w, n_total, n_chunks, r
         mu, _ = D.find_mu([part], n_chunks, w.electrons_per_atom * n_total, w.kT, group=group, device="cuda")
     n_again = mka.mka_sweep_density(sw, plan, mu, w.kT, rho.data_ptr())
     tot = D.totals([part], n_chunks, mu, w.kT, group=group, device="cuda")
-    return {"mu": mu, "resolved_atoms": n_again, **tot}
+    out = {"mu": mu, "resolved_atoms": n_again, **tot}
+    if F is not None:
+        out["forces_resolved_atoms"] = mka.mka_sweep_forces(sw, plan, mu, w.kT, F.data_ptr())
+    return out
 
 
 def full_fp64(mka, torch, D, sysh, w, a0, a1, N, n_chunks, B, win, kp, slices, rho_head, res_head, stream, group,
@@ -467,7 +512,7 @@ def full_fp64(mka, torch, D, sysh, w, a0, a1, N, n_chunks, B, win, kp, slices, r
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kms = []
     t0.record(stream)
-    res = sweep_flow(mka, torch, D, sysh, plan, sw, slices, B, w, N, n_chunks, rho, stream, group, kms)
+    res = sweep_flow(mka, torch, D, sysh, plan, sw, slices, B, w, N, n_chunks, rho, stream, group, kms, F)
     t1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(t0.elapsed_time(t1), "cuda")
@@ -526,18 +571,23 @@ def main():
     sample = np.sort(rng.choice(np.arange(a0, a1), min(4096, a1 - a0), replace=False)).astype(np.int64)
     tune = (mka.mka_autotune(sysh, prm, sample, w.electrons_per_atom * len(sample), w.kT, tune_cache, sp)
             if not args.no_autotune else mka.tuning())
+    if not args.batch and not args.no_autotune:   # the batch size from a measured search as well
+        cands = [b for b in (16384, 32768, 65536, 131072) if b <= max(16384, a1 - a0)]
+        B = mka.mka_autotune_batch(sysh, prm, tune, cands, a0, w.electrons_per_atom, w.kT, tune_cache, sp)
     plan = mka.mka_plan_create(sysh, B, prm, tune, sp)
     mu_s, win, max_in_win = sample_window(mka, plan, sample, w, args.window)
 
     # sweep sized for the free memory: rho [n_blocks][16] FP64 beside it
     nblk = int(mka.mka_system_info(sysh)["nnzb"] * (a1 - a0) / N) + 1
     free = torch.cuda.mem_get_info()[0]
-    fixed = 8 * 16 * nblk * 2 + 16 * 4 * (a1 - a0) * w.nu + (12 << 30)
+    # rho, the occupied parts of rho and pi, the forces' block sums, the levels, 12 GiB for the rest
+    fixed = 8 * 16 * nblk * 3 + 8 * 3 * nblk + 16 * 4 * (a1 - a0) * w.nu + 8 * 3 * N + (12 << 30)
     kp_fit = int((free - fixed) // (8 * 16 * nblk))
     kp = max(1, min(w.nu, max_in_win + 2, kp_fit))
-    sw = mka.mka_sweep_create(sysh, a0, a1, w.nu, win[0], win[1], kp, args.chunk_atoms, sp)
+    sw = mka.mka_sweep_create(sysh, a0, a1, w.nu, win[0], win[1], kp, args.chunk_atoms, sp, with_forces=True)
     nblk = mka.mka_sweep_info(sw)["n_blocks"]
     rho = torch.empty(nblk * 16, dtype=torch.float64, device="cuda")
+    F = torch.empty(3 * N, dtype=torch.float64, device="cuda")
     slices = step_slices(a0, a1, args.steps)
 
     # warm-up: the first W slices through the same path (captures every batch shape's graph)
@@ -558,7 +608,7 @@ def main():
     clocks.start()
     torch.cuda.nvtx.range_push("timed_sweep")
     t0.record(stream)
-    res = sweep_flow(mka, torch, D, sysh, plan, sw, slices, B, w, N, n_chunks, rho, stream, group, kms)
+    res = sweep_flow(mka, torch, D, sysh, plan, sw, slices, B, w, N, n_chunks, rho, stream, group, kms, F)
     t1.record(stream)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
@@ -568,6 +618,27 @@ def main():
     rank_barrier()
     value = 4 * N / (ms / 1e3)
     stored, overflow = mka.mka_sweep_status(sw)
+
+    # forces of every atom at the global mu (in the timed region, Eq. EQ-WORK-FLOW's last step); after it, the
+    # forces alone timed again, and the density of states of all 4.03e7 columns on a grid around mu
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    mka.mka_sweep_forces(sw, plan, res["mu"], w.kT, F.data_ptr())
+    f1.record(stream)
+    torch.cuda.synchronize()
+    Fh = F.view(-1, 3)
+    forces = {"seconds": f0.elapsed_time(f1) / 1e3, "resolved_atoms": res["forces_resolved_atoms"],
+              "max_abs_eV_per_A": float(Fh.abs().max().item()),
+              "max_abs_sum_eV_per_A": float(Fh.sum(0).abs().max().item()) if world == 1 else None}
+    del Fh
+    e_ptr, w_ptr = mka.mka_sweep_device_levels(sw)
+    grid = np.linspace(res["mu"] - 2.0, res["mu"] + 2.0, 41)
+    t_dos = time.perf_counter()
+    dos = mka.mka_dos(e_ptr, w_ptr, 4 * (a1 - a0) * w.nu, grid, w.kT, sp)
+    t_dos = time.perf_counter() - t_dos
+    dos_rec = {"seconds": t_dos, "energies_eV": [float(grid[0]), float(grid[-1]), len(grid)], "eta_eV": w.kT,
+               "states_per_eV_per_atom_at_mu": float(dos[20] / (a1 - a0)),
+               "min_states_per_eV_per_atom": float(dos.min() / (a1 - a0))}
 
     # ρ on sampled atoms of the rank against the oracle at the global mu (FP64 oracle on the stored values)
     # is a test (tests/test_gpu_sweep.py); here: the stored rho of a few atoms for the record
@@ -596,7 +667,10 @@ def main():
             mu_e, _ = D.find_mu([part], n_chunks, w.electrons_per_atom * N, w.kT, group=group, device="cuda")
         mka.mka_sweep_density(sw, plan, mu_e, w.kT, rho.data_ptr())
         tot_e = D.totals([part], n_chunks, mu_e, w.kT, group=group, device="cuda")
-        d2h = 0
+        mka.mka_sweep_forces(sw, plan, mu_e, w.kT, F.data_ptr())
+        Fhost = torch.empty(F.numel(), dtype=torch.float64, pin_memory=True)
+        Fhost.copy_(F)
+        d2h = 8 * F.numel()
         for o in range(0, rho.numel(), piece):
             n = min(piece, rho.numel() - o)
             host[:n].copy_(rho[o:o + n])
@@ -604,6 +678,7 @@ def main():
         torch.cuda.synchronize()
         rank_barrier()
         te = max_over_ranks(time.perf_counter() - te, "cuda")
+        del Fhost
         e2e = {"value": 4 * N / te, "unit": "columns/s", "h2d_bytes_per_step": h2d // args.steps,
                "d2h_bytes_per_step": (d2h + 24) // args.steps, "mu": mu_e,
                "same_mu_as_timed": mu_e == res["mu"], "same_e_band": tot_e["e_band"] == res["e_band"]}
@@ -614,7 +689,7 @@ def main():
                    "e_band_eV_per_atom": res["e_band"] / N, "e_band_levels_eV_per_atom": res["e_band_levels"] / N,
                    "n_electrons": res["n_electrons"], "n_electrons_target": w.electrons_per_atom * N,
                    "sample_mu_eV": mu_s, "window_eV": list(win), "kp": kp, "stored_atoms": stored,
-                   "overflow_atoms": overflow, "resolved_atoms": res["resolved_atoms"],
+                   "overflow_atoms": overflow, "resolved_atoms": res["resolved_atoms"], "forces": forces, "dos": dos_rec,
                    "sweep_bytes": mka.mka_sweep_info(sw)["bytes"], "rho_bytes": 8 * rho.numel()}
     mka.mka_sweep_destroy(sw)
     mka.mka_plan_destroy(plan)
@@ -651,6 +726,7 @@ def main():
             "max_abs_dE_eV_per_atom_vs_plain": max(abs(a - b) for a, b in zip(main_b["e_band"], prun["e_band"])) / B,
             "max_abs_dmu_eV_vs_plain": max(abs(a - b) for a, b in zip(main_b["mu"], prun["mu"]))})
         mka.mka_plan_destroy(prun["plan"])
+        learn_info["fresh_seed_evaluation"] = learned_eval(mka, torch, net)
     other = None
     if form != "fp64" and not args.no_fp64_compare:
         frun = run_form(mka, torch, sysh, w, "fp64", B, batch_atoms, n_steps_b, 1, stream, tune_cache, rank,
@@ -698,7 +774,7 @@ def main():
             "config": {"workload": workload_desc(args.workload, w, N),
                        "form": f"{form}{'+learned' if learned else ''}, {storage}-stored H and S",
                        "step": f"one slice of {len(slices[0])} atoms through plan batches of {B} atoms into the "
-                               "sweep; after the last, mu over all columns, rho on the whole pattern, energies",
+                               "sweep; after the last, mu over all columns, rho on the whole pattern, energies, forces",
                        "atoms_per_step": len(slices[0]), "batch_atoms": B,
                        "l2": "inputs larger than L2 (H, S, levels and rho pieces of the whole system in HBM)",
                        "tuning": {"threads": tune.threads, "ctas_per_sm": tune.ctas_per_sm,
