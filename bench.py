@@ -25,6 +25,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -169,6 +170,12 @@ def local_flops(tree, pos, row_ptr, col, atoms, R):
     return m_c, nnz_c
 
 
+def reduced_flops(nu):
+    """FLOPs of one column's reduced solve: Cholesky nu^3/3, congruence 2 nu^3, tridiagonalisation 2 nu^3,
+    Q 4 nu^3/3, Q Z 2 nu^3, L^-T nu^3; QL eigenvalues, inverse iteration and outputs about 47 nu^2."""
+    return 26.0 / 3.0 * nu ** 3 + 47.0 * nu ** 2
+
+
 def column_flops(m, nnz, nu, cg_it, n_pattern_rows):
     """Algorithmic FLOPs of one column, counted as plain arithmetic: the products of the CG and
     the basis, CG vector work, one Gram-Schmidt pass per vector (coefficients and update), norms,
@@ -178,7 +185,7 @@ def column_flops(m, nnz, nu, cg_it, n_pattern_rows):
     gs = 2.0 * m * nu * (nu - 1)                          # one pass of dots + updates per new vector
     norms = 4.0 * m * nu                                  # S-norm and scaling per vector
     proj = 4.0 * m * nu * nu                              # U^T K and U^T (S U)
-    red = 12.3 * nu ** 3                                  # Cholesky, two triangular solves, eig, back-transform
+    red = reduced_flops(nu)                               # the reduced generalized eigensolve
     out = 4.0 * nu * nu                                   # V_j and (S V)_j
     return spmv + cg_vec + gs + norms + proj + red + out
 
@@ -247,15 +254,38 @@ def cpu_baseline(w, pos, box, budget_s=20.0):
                              for i in range(cores) if len(extra[i::cores])])
             dt += time.perf_counter() - t1
             n_at += n_more
+    with oracle_pool(mp, 1) as pool:                  # one core: one process, one BLAS thread
+        pool.map(_work, [(pos, box, w.sk, w.R, [0], 2, 1, "fp64", 1e-13)])
+        one = np.sort(rng.choice(pos.shape[0], 2, replace=False))
+        t0 = time.perf_counter()
+        pool.map(_work, [(pos, box, w.sk, w.R, one, w.p, w.q, "fp64", 1e-13)])
+        dt1 = time.perf_counter() - t0
     return {"value": 4 * n_at / dt, "unit": "columns/s", "cores": cores, "kind": "oracle",
             "sample": f"{n_at} random atoms ({4 * n_at} columns) of {w.name}, FP64 numpy oracle, "
-                      f"one spawn process per core, one BLAS thread each"}
+                      f"one spawn process per core, one BLAS thread each",
+            "single_core": {"value": 4 * len(one) / dt1, "unit": "columns/s", "cores": 1,
+                            "sample": f"{len(one)} random atoms ({4 * len(one)} columns), one process, one BLAS thread"},
+            "cpu": cpu_model()}
+
+
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (x86: model name; Arm: implementer and part)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.machine()
+    names = [l.split(":", 1)[1].strip() for l in info if l.lower().startswith("model name")]
+    if names:
+        return f"{names[0]} x {len(names)}"
+    parts = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU part")]
+    impl = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU implementer")]
+    return f"{platform.machine()} implementer {impl[0] if impl else '?'} part {parts[0] if parts else '?'} x {len(parts)}"
 
 
 def flops_split(m, nnz, nu, cg_it, n_pattern_rows):
-    """Algorithmic (vector work, reduced solve) FLOPs of one column: the reduced solve is 12.3 nu^3."""
+    """Algorithmic (vector work, reduced solve) FLOPs of one column."""
     total = column_flops(m, nnz, nu, cg_it, n_pattern_rows)
-    red = 12.3 * nu ** 3
+    red = reduced_flops(nu)
     return total - red, red
 
 
@@ -758,8 +788,8 @@ def main():
                             "atoms_kernel", "cluster, CG, Krylov basis and projection, counted as plain (not pair) arithmetic",
                             sms, mhz)
     roofline_red = alu_roofline(float(np.mean(a_r)), 4 * B, red_ms / 1e3, "fp64", "reduced_kernel",
-                                "Cholesky, congruence, tridiagonalisation, QL with vectors, back-transform, "
-                                "outputs: 12.3 nu^3 FLOP per column", sms, mhz)
+                                "Cholesky, congruence, tridiagonalisation, QL eigenvalues, inverse iteration, "
+                                "back-transform, outputs: 26/3 nu^3 + 47 nu^2 FLOP per column", sms, mhz)
     if form == "mixed":   # DRAM bytes per launch from the profiler capture (null once the kernel has changed)
         roofline["traffic"] = captured_traffic("atoms_kernel", B)
         roofline_red["traffic"] = captured_traffic("reduced_kernel", 4 * B)

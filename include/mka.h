@@ -213,7 +213,7 @@ mka_status mka_solve_columns(mka_system* sys, const int64_t* atoms, int64_t n_se
  *               than `max_cluster_atoms` atoms)
  * Nothing for rho / G is kept (keep_vectors = 0 in effect).
  * Work memory (the work-queue counter, the atom list of a chunk, the chunk's
- * reduced problems, 8 (2 nu^2 + 2 nu) bytes per column, and one work slot per
+ * reduced problems, 8 (3 nu^2 + 2 nu) bytes per column, and one work slot per
  * CTA of about 8 (2 (p+q) + 2) x 4 max_cluster_atoms x 4 bytes) comes from one
  * file-scope device array of MKA_STATIC_SCRATCH_BYTES; the selection runs in
  * chunks sized to fit. The call returns MKA_ERR_INVALID_ARG, with a message,

@@ -140,8 +140,9 @@ struct AtomsLaunchArgs {
 };
 
 // Per-column doubles of the reduced-problem buffer: H_r and S_r (nu x nu each), then the
-// row j of U and of S U (nu each).
-__host__ __device__ constexpr size_t red_block_doubles(int nu) { return (size_t)2 * nu * nu + (size_t)2 * nu; }
+// row j of U and of S U (nu each), then nu x nu of scratch for the reduced kernel (the
+// eigenvectors of the tridiagonal matrix).
+__host__ __device__ constexpr size_t red_block_doubles(int nu) { return (size_t)3 * nu * nu + (size_t)2 * nu; }
 // Per-column doubles of the kept reduced solution: C (nu x nu, columns in ascending order of
 // eps) and the row V_j = (row j of U) C; rho_ij = U_i . (C diag(f) V_j).
 __host__ __device__ constexpr size_t kept_block_doubles(int nu) { return (size_t)nu * nu + (size_t)nu; }

@@ -4,8 +4,9 @@
 // S_r = U^T S U (formed explicitly, so that a basis that is only nearly S-orthonormal
 // still gives the Galerkin pencil of its span) and solves the generalized eigenproblem
 // H_r c = eps S_r c (Eq. EQ-SUB-EIG-VEC): Cholesky S_r = L L^T, A = L^{-1} H_r L^{-T},
-// Householder tridiagonalisation A = Q T Q^T, implicit-shift QL on T with the rotations
-// accumulated into Z = Q, C = L^{-T} Z. The outputs of a column are its levels eps_alpha
+// Householder tridiagonalisation A = Q T Q^T, the eigenvalues of T by the implicit-shift QL
+// method, the eigenvectors Z of T by inverse iteration (re-orthogonalised within clusters of
+// close eigenvalues), C = L^{-T} Q Z. The outputs of a column are its levels eps_alpha
 // in ascending order, w_alpha = V_{j alpha} (S V)_{j alpha} with V = U C (Eq. EQ-DM's
 // weights), and, when vectors are kept, C and the row V_j = (row j of U) C in the same order:
 // rho_ij = sum_alpha f_alpha V_i alpha V_j alpha = U_i . (C diag(f) V_j) and G_ij(z) likewise,
@@ -27,7 +28,7 @@ namespace mka {
 namespace {
 
 enum : int { RS_OK = 0, RS_NOT_SPD = MKA_ERR_NOT_SPD, RS_BREAKDOWN = MKA_ERR_BREAKDOWN };
-constexpr int kSmallNu = 64;
+constexpr int kTinyNu = 32, kSmallNu = 64;
 
 struct RedArgs {
   double* blk;               // [groups][red_block_doubles(nu)][32], in place
@@ -41,7 +42,8 @@ struct RedArgs {
   int64_t col0;
 };
 
-// Element (i, j) of the lane's matrices: H_r / Z / C at (i nu + j), S_r / L at nu^2 + (i nu + j).
+// Element (i, j) of the lane's matrices: H_r / A / Q / C at (i nu + j), S_r / L at nu^2 + (i nu + j),
+// then row j of U and of S U, then the eigenvectors Z of T (and Q Z) at 2 nu^2 + 2 nu + (i nu + j).
 struct Lane {
   double* b;
   int nu;
@@ -49,6 +51,7 @@ struct Lane {
   __device__ double& S(int i, int j) const { return b[(size_t)(nu * nu + i * nu + j) * 32]; }
   __device__ double UJ(int n) const { return b[(size_t)(2 * nu * nu + n) * 32]; }
   __device__ double SUJ(int n) const { return b[(size_t)(2 * nu * nu + nu + n) * 32]; }
+  __device__ double& Z(int i, int j) const { return b[(size_t)(2 * nu * nu + 2 * nu + i * nu + j) * 32]; }
 };
 
 // S_r = L L^T in the lower triangle of S (right-looking); rdiag[k] = 1 / L_kk.
@@ -169,10 +172,9 @@ __device__ void lane_tridiag(const Lane& M, int n, double* d, double* e, double*
 }
 
 // Eigenvalues of the tridiagonal (d, e) by the implicit-shift QL method (Bowdler, Martin,
-// Reinsch & Wilkinson, Numer. Math. 11, 1968); each sweep's rotations, recorded in (rc, rs),
-// are then applied to the columns of Z (carrying the updated column down the sweep).
-// Rotation lengths from rsqrt(f^2 + g^2). False when an eigenvalue needs more than 60 sweeps.
-__device__ bool lane_tql(const Lane& M, int n, double* d, double* e, double* rc, double* rs) {
+// Reinsch & Wilkinson, Numer. Math. 11, 1968), in place on d (e is destroyed); rotation
+// lengths from rsqrt(f^2 + g^2). False when an eigenvalue needs more than 60 sweeps.
+__device__ bool lane_tql_values(int n, double* d, double* e) {
   for (int l = 0; l < n; ++l) {
     for (int iter = 0;; ++iter) {
       int m = l;
@@ -187,8 +189,7 @@ __device__ bool lane_tql(const Lane& M, int n, double* d, double* e, double* rc,
       g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
       double s = 1.0, c = 1.0, p = 0.0;
       bool early = false;
-      int i = m - 1;
-      for (; i >= l; --i) {
+      for (int i = m - 1; i >= l; --i) {
         const double f = s * e[i], b = c * e[i];
         const double t = f * f + g * g;
         if (t == 0.0) {
@@ -207,31 +208,126 @@ __device__ bool lane_tql(const Lane& M, int n, double* d, double* e, double* rc,
         p = s * r;
         d[i + 1] = g + p;
         g = c * r - b;
-        rc[i] = c;
-        rs[i] = s;
       }
       if (!early) {
         d[l] -= p;
         e[l] = g;
         e[m] = 0.0;
       }
-      const int i0 = early ? i + 1 : l;
-      for (int k = 0; k < n; ++k) {
-        double zi1 = M.H(k, m);
-        for (int ii = m - 1; ii >= i0; --ii) {
-          const double zi = M.H(k, ii);
-          M.H(k, ii + 1) = rs[ii] * zi + rc[ii] * zi1;
-          zi1 = rc[ii] * zi - rs[ii] * zi1;
-        }
-        M.H(k, i0) = zi1;
-      }
     }
   }
   return true;
 }
 
-// NUCAP bounds nu: the lane's vectors live in local memory sized NUCAP, so subspaces up to 64 take
-// the small instance and larger ones (up to MKA_MAX_NU) the large one.
+// One solve (T - lam I) x <- x of inverse iteration: Gaussian elimination with partial pivoting on
+// the tridiagonal (d, e), the right-hand side carried along, U kept in (u0, u1, u2) (diagonal and two
+// superdiagonals); a pivot that vanishes is replaced by `tiny`.
+__device__ void lane_tri_solve(int n, const double* d, const double* e, double lam, double tiny, double* x,
+                               double* u0, double* u1, double* u2) {
+  double a = d[0] - lam, bb = n > 1 ? e[0] : 0.0;   // the working row: a at column k, bb at k + 1
+  for (int k = 0; k + 1 < n; ++k) {
+    const double sub = e[k], dn = d[k + 1] - lam, sp = k + 2 < n ? e[k + 1] : 0.0;
+    if (fabs(a) >= fabs(sub)) {
+      const double mlt = a != 0.0 ? sub / a : 0.0;
+      u0[k] = a;
+      u1[k] = bb;
+      u2[k] = 0.0;
+      x[k + 1] -= mlt * x[k];
+      a = dn - mlt * bb;
+      bb = sp;
+    } else {                               // row k + 1 becomes the pivot row
+      const double mlt = a / sub;
+      u0[k] = sub;
+      u1[k] = dn;
+      u2[k] = sp;
+      const double xk = x[k];
+      x[k] = x[k + 1];
+      x[k + 1] = xk - mlt * x[k + 1];
+      a = bb - mlt * dn;
+      bb = -mlt * sp;
+    }
+  }
+  u0[n - 1] = a;
+  for (int k = 0; k < n; ++k)
+    if (u0[k] == 0.0) u0[k] = tiny;
+  x[n - 1] /= u0[n - 1];
+  if (n >= 2) x[n - 2] = (x[n - 2] - u1[n - 2] * x[n - 1]) / u0[n - 2];
+  for (int k = n - 3; k >= 0; --k) x[k] = (x[k] - u1[k] * x[k + 1] - u2[k] * x[k + 2]) / u0[k];
+}
+
+// The eigenvectors of the tridiagonal (d, e) for its eigenvalues lam[0..n) (ascending) by inverse
+// iteration (Wilkinson; the scheme of LAPACK's dstein): from a fixed quasi-random start, two solves
+// of (T - lam_a I) x = x, each followed by modified Gram-Schmidt against the vectors of the same
+// cluster already found (eigenvalues closer than 1e-3 ||T||_1 to their neighbour) and
+// normalisation; stored as the columns of Z.
+__device__ void lane_tri_vectors(const Lane& M, int n, const double* d, const double* e, const double* lam,
+                                 double* x, double* u0, double* u1, double* u2) {
+  double tn = 0.0;
+  for (int k = 0; k < n; ++k)
+    tn = fmax(tn, fabs(d[k]) + (k + 1 < n ? fabs(e[k]) : 0.0) + (k > 0 ? fabs(e[k - 1]) : 0.0));
+  const double ortol = 1e-3 * tn, tiny = 2.2204460492503131e-16 * (tn > 0.0 ? tn : 1.0);
+  int cs = 0;
+  for (int a = 0; a < n; ++a) {
+    if (a == 0 || lam[a] - lam[a - 1] > ortol) cs = a;
+    for (int i = 0; i < n; ++i) {        // start: an additive-recurrence (golden ratio) sequence in [0.5, 1.5)
+      const double t = 0.7548776662466927 * (i + 1) + 0.5698402909980532 * (a + 1);
+      x[i] = 0.5 + (t - floor(t));
+    }
+    for (int it = 0; it < 2; ++it) {
+      lane_tri_solve(n, d, e, lam[a], tiny, x, u0, u1, u2);
+      for (int b = cs; b < a; ++b) {
+        double dot = 0.0;
+        for (int i = 0; i < n; ++i) dot += M.Z(i, b) * x[i];
+        for (int i = 0; i < n; ++i) x[i] -= dot * M.Z(i, b);
+      }
+      double s2 = 0.0;
+      for (int i = 0; i < n; ++i) s2 += x[i] * x[i];
+      const double sc = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+      for (int i = 0; i < n; ++i) x[i] *= sc;
+    }
+    for (int i = 0; i < n; ++i) M.Z(i, a) = x[i];
+  }
+}
+
+// C = L^{-T} Q Z, four columns at a time: first Q Z into Z (each block of four columns of Z read
+// into x4 before it is overwritten), then the back substitution with L^T into H.
+template <int NUCAP>
+__device__ void lane_back_transform(const Lane& M, int n, const double* rdiag, double (*x4)[NUCAP]) {
+  for (int a0 = 0; a0 < n; a0 += 4) {
+    const int na = min(4, n - a0);
+    for (int r = 0; r < 4; ++r)
+      for (int k = 0; k < n; ++k) x4[r][k] = r < na ? M.Z(k, a0 + r) : 0.0;
+    for (int i = 0; i < n; ++i) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int k = 0; k < n; ++k) {
+        const double q = M.H(i, k);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r] += q * x4[r][k];
+      }
+      for (int r = 0; r < na; ++r) M.Z(i, a0 + r) = acc[r];
+    }
+  }
+  for (int a0 = 0; a0 < n; a0 += 4) {   // C = L^{-T} (Q Z), by columns, kept in x4
+    const int na = min(4, n - a0);
+    for (int i = n - 1; i >= 0; --i) {
+      double s[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) s[r] = r < na ? M.Z(i, a0 + r) : 0.0;
+      for (int k = i + 1; k < n; ++k) {
+        const double l = M.S(k, i);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) s[r] -= l * x4[r][k];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) x4[r][i] = s[r] * rdiag[i];
+    }
+    for (int r = 0; r < na; ++r)
+      for (int i = 0; i < n; ++i) M.H(i, a0 + r) = x4[r][i];
+  }
+}
+
+// NUCAP bounds nu: the lane's vectors live in local memory sized NUCAP, so subspaces up to 32 and 64
+// take the small instances and larger ones (up to MKA_MAX_NU) the large one.
 template <int NUCAP>
 __global__ void __launch_bounds__(128) reduced_kernel(const RedArgs A) {
   const int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -239,6 +335,7 @@ __global__ void __launch_bounds__(128) reduced_kernel(const RedArgs A) {
   const int nu = A.nu;
   const Lane M{A.blk + (size_t)(col >> 5) * red_block_doubles(nu) * 32 + (col & 31), nu};
   double d[NUCAP], e[NUCAP], rdiag[NUCAP], p[NUCAP], tau[NUCAP], v[NUCAP];
+  double x4[4][NUCAP];
   int rank[NUCAP];
   const int n = A.nu_eff[col];
   const int st_in = A.status[col];
@@ -247,21 +344,24 @@ __global__ void __launch_bounds__(128) reduced_kernel(const RedArgs A) {
   if (ok) {
     lane_congruence(M, n, rdiag, v);
     lane_tridiag(M, n, d, e, p, tau, v);
-    ok = lane_tql(M, n, d, e, p, tau);   // p, tau reused as the rotation record
+    for (int k = 0; k < n; ++k) {      // the eigenvalues from copies: T stays for the eigenvectors
+      p[k] = d[k];
+      tau[k] = e[k];
+    }
+    ok = lane_tql_values(n, p, tau);
   }
   if (ok) {
-    for (int a = 0; a < n; ++a) {      // C = L^{-T} Z, column a by back substitution (kept in v)
-      for (int i = n - 1; i >= 0; --i) {
-        double s = M.H(i, a);
-        for (int k = i + 1; k < n; ++k) s -= M.S(k, i) * v[k];
-        v[i] = s * rdiag[i];
-      }
-      for (int i = 0; i < n; ++i) M.H(i, a) = v[i];
+    for (int a = 1; a < n; ++a) {      // ascending
+      const double t = p[a];
+      int b = a - 1;
+      for (; b >= 0 && p[b] > t; --b) p[b + 1] = p[b];
+      p[b + 1] = t;
     }
+    lane_tri_vectors(M, n, d, e, p, v, x4[0], x4[1], x4[2]);
+    lane_back_transform<NUCAP>(M, n, rdiag, x4);
     for (int a = 0; a < n; ++a) {
-      int r = 0;
-      for (int k = 0; k < n; ++k) r += (d[k] < d[a]) || (d[k] == d[a] && k < a);
-      rank[a] = r;
+      d[a] = p[a];
+      rank[a] = a;
     }
   }
   int stc = st_in;
@@ -322,7 +422,8 @@ mka_status reduced_launch(double* blk, int64_t n_cols, int nu, int32_t* status, 
   A.col0 = col0;
   const int threads = 128;
   const unsigned blocks = (unsigned)((n_cols + threads - 1) / threads);
-  if (nu <= kSmallNu) reduced_kernel<kSmallNu><<<blocks, threads, 0, st>>>(A);
+  if (nu <= kTinyNu) reduced_kernel<kTinyNu><<<blocks, threads, 0, st>>>(A);
+  else if (nu <= kSmallNu) reduced_kernel<kSmallNu><<<blocks, threads, 0, st>>>(A);
   else reduced_kernel<MKA_MAX_NU><<<blocks, threads, 0, st>>>(A);
   count_launches();
   MKA_CUDA_TRY(cudaGetLastError());
