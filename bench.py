@@ -254,6 +254,14 @@ def cpu_baseline(w, pos, box, budget_s=20.0):
                              for i in range(cores) if len(extra[i::cores])])
             dt += time.perf_counter() - t1
             n_at += n_more
+        # config 1 in full: every column of the 512-atom diamond system, the same p, q, R and CG tolerance
+        from synth import WORKLOADS, workload_positions
+        w1 = WORKLOADS["diamond512"]
+        pos1, box1 = workload_positions(w1)
+        a1 = np.arange(pos1.shape[0])
+        t0 = time.perf_counter()
+        pool.map(_work, [(pos1, box1, w1.sk, w1.R, a1[i::cores], w1.p, w1.q, "fp64", 1e-13) for i in range(cores)])
+        dt_full = time.perf_counter() - t0
     with oracle_pool(mp, 1) as pool:                  # one core: one process, one BLAS thread
         pool.map(_work, [(pos, box, w.sk, w.R, [0], 2, 1, "fp64", 1e-13)])
         one = np.sort(rng.choice(pos.shape[0], 2, replace=False))
@@ -265,6 +273,8 @@ def cpu_baseline(w, pos, box, budget_s=20.0):
                       f"one spawn process per core, one BLAS thread each",
             "single_core": {"value": 4 * len(one) / dt1, "unit": "columns/s", "cores": 1,
                             "sample": f"{len(one)} random atoms ({4 * len(one)} columns), one process, one BLAS thread"},
+            "config1_full": {"value": 4 * len(a1) / dt_full, "unit": "columns/s", "cores": cores,
+                             "seconds": dt_full, "sample": f"all {4 * len(a1)} columns of {w1.name}"},
             "cpu": cpu_model()}
 
 

@@ -284,9 +284,10 @@ def test_mixed_form_against_oracle_on_stored_values(lib, storage):
         assert np.all(lv["status"] == 0)
         oe, ow = osys.stack_eps_w(ores)
         print(f"mixed {storage}: max|d eps| {np.abs(lv['eps'] - oe).max():.2e}  max|d w| {np.abs(lv['w'] - ow).max():.2e}")
-        # individual Ritz values with tiny weight move under a 1e-7 change of the subspace without
-        # touching rho; the gates are rho, E and mu below, eps and w are only bounded loosely
-        assert np.abs(lv["eps"] - oe).max() < 1e-2 and np.abs(lv["w"] - ow).max() < 1e-3
+        # the mixed form's subspace differs from the FP64 form's by about 1e-7 (FP32 pairs, s_j to 1e-7 and
+        # refined); a Ritz value moves by at most about ||H|| times that (||H|| ~ 30 eV here) and a weight
+        # by a modest multiple of it: eps within 1e-5 eV and w within 5e-6 (observed 2e-6 and 5e-7)
+        assert np.abs(lv["eps"] - oe).max() < 1e-5 and np.abs(lv["w"] - ow).max() < 5e-6
         for mu in (0.3, 1.9):
             rho, e, n = gpu_density(mka, s, res, mu, w.kT)
             orho, oe_band, on = osys.density(ores, mu, w.kT)
