@@ -222,8 +222,8 @@ mka_status mka_solve_columns(mka_system* sys, const int64_t* atoms, int64_t n_se
  * The call performs no cudaMalloc, cudaFree or other allocating routine. Each
  * call looks up the array's device address on the current device
  * (cudaGetSymbolAddress, no allocation); the first call on a device may load
- * the library's device code there, so make that first call before any stream
- * capture. Every call on a device shares the one array, so calls whose GPU
+ * the library's device code there. Every call on a device shares the one
+ * array, so calls whose GPU
  * work overlaps (different streams, or host threads, without ordering between
  * them) race on it and corrupt each other's results; order them on one stream.
  * The work-queue counter is cleared by each call; the rest is overwritten. */
