@@ -3,7 +3,7 @@
 // Every column j ends its basis with the nu x nu projected matrices H_r = U^T H U and
 // S_r = U^T S U (formed explicitly, so that a basis that is only nearly S-orthonormal
 // still gives the Galerkin pencil of its span) and solves the generalized eigenproblem
-// H_r c = eps S_r c (Eq. EQ-SUB-EIG-VEC): Cholesky S_r = L L^T, A = L^{-1} H_r L^{-T},
+// H_r c = eps S_r c (Eq. EQ-SUB-EIG-VEC): Cholesky S_r = L L^T, A = L^{-1} H_r L^{-T} (lower triangle),
 // Householder tridiagonalisation A = Q T Q^T, the eigenvalues of T by the implicit-shift QL
 // method, the eigenvectors Z of T by inverse iteration (re-orthogonalised within clusters of
 // close eigenvalues), C = L^{-T} Q Z. The outputs of a column are its levels eps_alpha
@@ -72,36 +72,33 @@ __device__ bool lane_cholesky(const Lane& M, int n, double* rdiag) {
   return true;
 }
 
-// H <- L^{-1} H L^{-T} (full storage), symmetrised. `row` (n doubles, lane-local) holds the
-// row of L, then of A, that an inner loop reuses.
-__device__ void lane_congruence(const Lane& M, int n, const double* rdiag, double* row) {
-  for (int i = 0; i < n; ++i) {        // X = L^{-1} H, row i from rows 0..i-1
-    for (int k = 0; k < i; ++k) row[k] = M.S(i, k);
-    for (int j = 0; j < n; ++j) {
-      double v = M.H(i, j);
-      for (int k = 0; k < i; ++k) v -= row[k] * M.H(k, j);
-      M.H(i, j) = v * rdiag[i];
+// The lower triangle of A = L^{-1} H L^{-T} in place of H's, using the symmetry of H and A (n^3 / 2
+// FMAs): first the upper triangle of X = L^{-1} H over H's (row j from the rows above it), then A =
+// L^{-1} X^T column by column, the entries of column j above the diagonal taken from row j of A. `row`
+// and `col` (n doubles each, lane-local) hold the row of L and the column of A an inner loop reuses.
+__device__ void lane_congruence(const Lane& M, int n, const double* rdiag, double* row, double* col) {
+  for (int j = 0; j < n; ++j) {        // X(j, i), i >= j
+    for (int k = 0; k < j; ++k) row[k] = M.S(j, k);
+    for (int i = j; i < n; ++i) {
+      double v = M.H(j, i);
+      for (int k = 0; k < j; ++k) v -= row[k] * M.H(k, i);
+      M.H(j, i) = v * rdiag[j];
     }
   }
-  for (int i = 0; i < n; ++i)          // A = X L^{-T}, column j from columns 0..j-1
-    for (int j = 0; j < n; ++j) {
-      double v = M.H(i, j);
-      for (int k = 0; k < j; ++k) v -= row[k] * M.S(j, k);
-      v *= rdiag[j];
-      row[j] = v;
-      M.H(i, j) = v;
+  for (int j = 0; j < n; ++j) {        // A(i, j), i >= j
+    for (int k = 0; k < j; ++k) col[k] = M.H(j, k);
+    for (int i = j; i < n; ++i) {
+      double v = M.H(j, i);
+      for (int k = 0; k < i; ++k) v -= M.S(i, k) * col[k];
+      col[i] = v * rdiag[i];
     }
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < i; ++j) {
-      const double v = 0.5 * (M.H(i, j) + M.H(j, i));
-      M.H(i, j) = v;
-      M.H(j, i) = v;
-    }
+    for (int i = j; i < n; ++i) M.H(i, j) = col[i];
+  }
 }
 
-// Householder reduction T = Q^T A Q: diagonal d, off-diagonal e (e[k] couples k, k+1;
-// e[n-1] = 0); Q accumulated in place of A. v (n doubles, lane-local) holds the current
-// Householder vector.
+// Householder reduction T = Q^T A Q of A given by its lower triangle: diagonal d, off-diagonal e
+// (e[k] couples k, k+1; e[n-1] = 0); Q accumulated in place of A. v (n doubles, lane-local) holds
+// the current Householder vector.
 __device__ void lane_tridiag(const Lane& M, int n, double* d, double* e, double* p, double* tau, double* v) {
   for (int k = 0; k + 2 < n; ++k) {
     double s2 = 0.0;
@@ -121,17 +118,18 @@ __device__ void lane_tridiag(const Lane& M, int n, double* d, double* e, double*
     e[k] = alpha;
     tau[k] = tk;
     double pv = 0.0;
-    for (int i = k + 1; i < n; ++i) {                         // p = tk B v
+    for (int i = k + 1; i < n; ++i) {                         // p = tk B v, B from its lower triangle
       double acc = 0.0;
-      for (int j = k + 1; j < n; ++j) acc += M.H(i, j) * v[j];
+      for (int j = k + 1; j <= i; ++j) acc += M.H(i, j) * v[j];
+      for (int j = i + 1; j < n; ++j) acc += M.H(j, i) * v[j];
       p[i] = tk * acc;
       pv += p[i] * v[i];
     }
     const double kc = 0.5 * tk * pv;
     for (int i = k + 1; i < n; ++i) p[i] -= kc * v[i];        // w = p - kc v
-    for (int i = k + 1; i < n; ++i) {                         // B -= v w^T + w v^T
+    for (int i = k + 1; i < n; ++i) {                         // B -= v w^T + w v^T, lower triangle
       const double vi = v[i], wi = p[i];
-      for (int j = k + 1; j < n; ++j) M.H(i, j) -= vi * p[j] + wi * v[j];
+      for (int j = k + 1; j <= i; ++j) M.H(i, j) -= vi * p[j] + wi * v[j];
     }
   }
   if (n >= 2) {
@@ -219,49 +217,61 @@ __device__ bool lane_tql_values(int n, double* d, double* e) {
   return true;
 }
 
-// One solve (T - lam I) x <- x of inverse iteration: Gaussian elimination with partial pivoting on
-// the tridiagonal (d, e), the right-hand side carried along, U kept in (u0, u1, u2) (diagonal and two
-// superdiagonals); a pivot that vanishes is replaced by `tiny`.
-__device__ void lane_tri_solve(int n, const double* d, const double* e, double lam, double tiny, double* x,
-                               double* u0, double* u1, double* u2) {
+// Gaussian elimination with partial pivoting of the tridiagonal T - lam I (d, e): the multipliers and
+// row interchanges in (mlt, swp), U as reciprocal pivots r0 and the two superdiagonals (u1, u2); a
+// pivot that vanishes is replaced by `tiny`. One division per row.
+__device__ void lane_tri_factor(int n, const double* d, const double* e, double lam, double tiny, double* r0,
+                                double* u1, double* u2, double* mlt, int* swp) {
   double a = d[0] - lam, bb = n > 1 ? e[0] : 0.0;   // the working row: a at column k, bb at k + 1
   for (int k = 0; k + 1 < n; ++k) {
     const double sub = e[k], dn = d[k + 1] - lam, sp = k + 2 < n ? e[k + 1] : 0.0;
     if (fabs(a) >= fabs(sub)) {
-      const double mlt = a != 0.0 ? sub / a : 0.0;
-      u0[k] = a;
+      const double ra = 1.0 / (a != 0.0 ? a : tiny);
+      mlt[k] = sub * ra;
+      swp[k] = 0;
+      r0[k] = ra;
       u1[k] = bb;
       u2[k] = 0.0;
-      x[k + 1] -= mlt * x[k];
-      a = dn - mlt * bb;
+      a = dn - mlt[k] * bb;
       bb = sp;
     } else {                               // row k + 1 becomes the pivot row
-      const double mlt = a / sub;
-      u0[k] = sub;
+      const double rs = 1.0 / sub;
+      mlt[k] = a * rs;
+      swp[k] = 1;
+      r0[k] = rs;
       u1[k] = dn;
       u2[k] = sp;
-      const double xk = x[k];
-      x[k] = x[k + 1];
-      x[k + 1] = xk - mlt * x[k + 1];
-      a = bb - mlt * dn;
-      bb = -mlt * sp;
+      a = bb - mlt[k] * dn;
+      bb = -mlt[k] * sp;
     }
   }
-  u0[n - 1] = a;
-  for (int k = 0; k < n; ++k)
-    if (u0[k] == 0.0) u0[k] = tiny;
-  x[n - 1] /= u0[n - 1];
-  if (n >= 2) x[n - 2] = (x[n - 2] - u1[n - 2] * x[n - 1]) / u0[n - 2];
-  for (int k = n - 3; k >= 0; --k) x[k] = (x[k] - u1[k] * x[k + 1] - u2[k] * x[k + 2]) / u0[k];
+  r0[n - 1] = 1.0 / (a != 0.0 ? a : tiny);
+}
+
+// x <- (T - lam I)^{-1} x from the factors of lane_tri_factor: the row operations, then back substitution.
+__device__ void lane_tri_apply(int n, const double* r0, const double* u1, const double* u2, const double* mlt,
+                               const int* swp, double* x) {
+  for (int k = 0; k + 1 < n; ++k) {
+    if (swp[k]) {
+      const double xk = x[k];
+      x[k] = x[k + 1];
+      x[k + 1] = xk - mlt[k] * x[k + 1];
+    } else {
+      x[k + 1] -= mlt[k] * x[k];
+    }
+  }
+  x[n - 1] *= r0[n - 1];
+  if (n >= 2) x[n - 2] = (x[n - 2] - u1[n - 2] * x[n - 1]) * r0[n - 2];
+  for (int k = n - 3; k >= 0; --k) x[k] = (x[k] - u1[k] * x[k + 1] - u2[k] * x[k + 2]) * r0[k];
 }
 
 // The eigenvectors of the tridiagonal (d, e) for its eigenvalues lam[0..n) (ascending) by inverse
 // iteration (Wilkinson; the scheme of LAPACK's dstein): from a fixed quasi-random start, two solves
-// of (T - lam_a I) x = x, each followed by modified Gram-Schmidt against the vectors of the same
+// of (T - lam_a I) x = x with one factorisation, each followed by modified Gram-Schmidt against the vectors of the same
 // cluster already found (eigenvalues closer than 1e-3 ||T||_1 to their neighbour) and
 // normalisation; stored as the columns of Z.
 __device__ void lane_tri_vectors(const Lane& M, int n, const double* d, const double* e, const double* lam,
-                                 double* x, double* u0, double* u1, double* u2) {
+                                 double* x, double* r0, double* u1, double* u2, double* mlt, int* swp) {
   double tn = 0.0;
   for (int k = 0; k < n; ++k)
     tn = fmax(tn, fabs(d[k]) + (k + 1 < n ? fabs(e[k]) : 0.0) + (k > 0 ? fabs(e[k - 1]) : 0.0));
@@ -273,8 +283,9 @@ __device__ void lane_tri_vectors(const Lane& M, int n, const double* d, const do
       const double t = 0.7548776662466927 * (i + 1) + 0.5698402909980532 * (a + 1);
       x[i] = 0.5 + (t - floor(t));
     }
+    lane_tri_factor(n, d, e, lam[a], tiny, r0, u1, u2, mlt, swp);
     for (int it = 0; it < 2; ++it) {
-      lane_tri_solve(n, d, e, lam[a], tiny, x, u0, u1, u2);
+      lane_tri_apply(n, r0, u1, u2, mlt, swp, x);
       for (int b = cs; b < a; ++b) {
         double dot = 0.0;
         for (int i = 0; i < n; ++i) dot += M.Z(i, b) * x[i];
@@ -342,7 +353,7 @@ __global__ void __launch_bounds__(128) reduced_kernel(const RedArgs A) {
   bool ok = st_in == RS_OK && n > 0 && n <= nu;
   if (ok) ok = lane_cholesky(M, n, rdiag);
   if (ok) {
-    lane_congruence(M, n, rdiag, v);
+    lane_congruence(M, n, rdiag, v, p);
     lane_tridiag(M, n, d, e, p, tau, v);
     for (int k = 0; k < n; ++k) {      // the eigenvalues from copies: T stays for the eigenvectors
       p[k] = d[k];
@@ -357,7 +368,7 @@ __global__ void __launch_bounds__(128) reduced_kernel(const RedArgs A) {
       for (; b >= 0 && p[b] > t; --b) p[b + 1] = p[b];
       p[b + 1] = t;
     }
-    lane_tri_vectors(M, n, d, e, p, v, x4[0], x4[1], x4[2]);
+    lane_tri_vectors(M, n, d, e, p, v, x4[0], x4[1], x4[2], x4[3], rank);
     lane_back_transform<NUCAP>(M, n, rdiag, x4);
     for (int a = 0; a < n; ++a) {
       d[a] = p[a];

@@ -40,8 +40,8 @@ struct BisState {
   double lo, hi, target, kT, tol, last, iters, pad;
 };
 
-__device__ __forceinline__ double fermi_f(double x, double mu, double kT) {
-  const double y = (x - mu) / (2.0 * kT);
+__device__ __forceinline__ double fermi_f(double x, double mu, double r2kT) {   // r2kT = 1 / (2 kT)
+  const double y = (x - mu) * r2kT;
   if (y > 20.0) return 0.0;
   if (y < -20.0) return 1.0;
   return 0.5 * (1.0 - tanh(y));
@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(kChunkThreads) sweep_chunk_kernel(const ChunkA
     mu = 0.5 * (A.S->lo + A.S->hi);
     kT = A.S->kT;
   }
+  const double r2kT = 0.5 / kT;        // one division per thread, a product per level
   const int64_t gi = blockIdx.x;
   const int64_t g = A.chunk0 + gi;
   const int64_t lo = max(A.a0, g * A.chunk_atoms), hi = min(A.a1, (g + 1) * A.chunk_atoms);
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(kChunkThreads) sweep_chunk_kernel(const ChunkA
     const double wi = A.w[e];
     if (wi != 0.0) {
       const double x = A.eps[e];
-      const double f = fermi_f(x, mu, kT);
+      const double f = fermi_f(x, mu, r2kT);
       c += f * wi;
       if (A.e_levels) el += f * x * wi;
     }
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(256) sweep_rho_kernel(const RhoArgs A) {
     for (int i = lane; i < 4 * kp; i += 32) {
       const int c = i / kp, a = i % kp;
       const uint16_t* wn = A.win + 2 * (4 * la + c);
-      f[i] = a < wn[1] ? fermi_f(A.eps[(4 * la + c) * nu + wn[0] + a], A.mu, A.kT) : 0.0;
+      f[i] = a < wn[1] ? fermi_f(A.eps[(4 * la + c) * nu + wn[0] + a], A.mu, 0.5 / A.kT) : 0.0;
     }
     __syncwarp();
     const int64_t atom = A.a0 + la;
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(256) sweep_force_kernel(const ForceArgs A) {
       const int c = i / kp, a = i % kp;
       const uint16_t* wn = A.win + 2 * (4 * la + c);
       const double x = a < wn[1] ? A.eps[(4 * la + c) * nu + wn[0] + a] : 0.0;
-      const double fx = a < wn[1] ? fermi_f(x, A.mu, A.kT) : 0.0;
+      const double fx = a < wn[1] ? fermi_f(x, A.mu, 0.5 / A.kT) : 0.0;
       f[i] = fx;
       fe[i] = fx * x;
     }
