@@ -172,9 +172,9 @@ def local_flops(tree, pos, row_ptr, col, atoms, R):
 
 def reduced_flops(nu):
     """FLOPs of one column's reduced solve: Cholesky nu^3/3, congruence nu^3 (both triangles of the symmetric
-    products), tridiagonalisation 4 nu^3/3 (lower-triangle update), Q 4 nu^3/3, Q Z 2 nu^3, L^-T nu^3; QL
-    eigenvalues, inverse iteration and outputs about 47 nu^2."""
-    return 7.0 * nu ** 3 + 47.0 * nu ** 2
+    products), tridiagonalisation 4 nu^3/3 (lower-triangle update), Q's reflectors applied to the
+    eigenvectors 2 nu^3, L^-T nu^3; QL eigenvalues, inverse iteration and outputs about 47 nu^2."""
+    return 17.0 / 3.0 * nu ** 3 + 47.0 * nu ** 2
 
 
 def column_flops(m, nnz, nu, cg_it, n_pattern_rows):
@@ -800,7 +800,7 @@ def main():
                             sms, mhz)
     roofline_red = alu_roofline(float(np.mean(a_r)), 4 * B, red_ms / 1e3, "fp64", "reduced_kernel",
                                 "Cholesky, congruence, tridiagonalisation, QL eigenvalues, inverse iteration, "
-                                "back-transform, outputs: 7 nu^3 + 47 nu^2 FLOP per column", sms, mhz)
+                                "back-transform, outputs: 17/3 nu^3 + 47 nu^2 FLOP per column", sms, mhz)
     if form == "mixed":   # DRAM bytes per launch from the profiler capture (null once the kernel has changed)
         roofline["traffic"] = captured_traffic("atoms_kernel", B)
         roofline_red["traffic"] = captured_traffic("reduced_kernel", 4 * B)

@@ -725,8 +725,14 @@ __device__ __noinline__ void raw_chain_step(const TV* __restrict__ valH, const i
   __syncthreads();
 }
 
+// Resident CTAs per SM the register budget is cut for: the FP32 form at 256 threads runs five (48
+// registers: 124.8 against 132.8 ms per 16,384 atoms at four, the kernel waits on memory and gains
+// from the extra warps; six at 40 registers spill and lose); otherwise 1024 threads per SM.
+template <typename T, int NT>
+constexpr int atoms_min_blocks() { return (sizeof(T) == 4 && NT == 256) ? 5 : 1024 / NT; }
+
 template <typename TV, typename T, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) atoms_kernel(const Args<TV> A) {
+__global__ void __launch_bounds__(NT, atoms_min_blocks<T, NT>()) atoms_kernel(const Args<TV> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ AtomState st;
   __shared__ double red[2 * kMaxWarps * 4];

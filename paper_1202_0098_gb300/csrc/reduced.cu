@@ -6,7 +6,7 @@
 // H_r c = eps S_r c (Eq. EQ-SUB-EIG-VEC): Cholesky S_r = L L^T, A = L^{-1} H_r L^{-T} (lower triangle),
 // Householder tridiagonalisation A = Q T Q^T, the eigenvalues of T by the implicit-shift QL
 // method, the eigenvectors Z of T by inverse iteration (re-orthogonalised within clusters of
-// close eigenvalues), C = L^{-T} Q Z. The outputs of a column are its levels eps_alpha
+// close eigenvalues), C = L^{-T} Q Z with Q applied as its reflectors. The outputs of a column are its levels eps_alpha
 // in ascending order, w_alpha = V_{j alpha} (S V)_{j alpha} with V = U C (Eq. EQ-DM's
 // weights), and, when vectors are kept, C and the row V_j = (row j of U) C in the same order:
 // rho_ij = sum_alpha f_alpha V_i alpha V_j alpha = U_i . (C diag(f) V_j) and G_ij(z) likewise,
@@ -97,8 +97,9 @@ __device__ void lane_congruence(const Lane& M, int n, const double* rdiag, doubl
 }
 
 // Householder reduction T = Q^T A Q of A given by its lower triangle: diagonal d, off-diagonal e
-// (e[k] couples k, k+1; e[n-1] = 0); Q accumulated in place of A. v (n doubles, lane-local) holds
-// the current Householder vector.
+// (e[k] couples k, k+1; e[n-1] = 0). Q = H_0 H_1 ... H_{n-3} is kept as its reflectors
+// H_k = I - tau[k] v_k v_k^T, v_k in column k below the diagonal (rows k+1..n-1). v (n doubles,
+// lane-local) holds the current Householder vector.
 __device__ void lane_tridiag(const Lane& M, int n, double* d, double* e, double* p, double* tau, double* v) {
   for (int k = 0; k + 2 < n; ++k) {
     double s2 = 0.0;
@@ -138,35 +139,6 @@ __device__ void lane_tridiag(const Lane& M, int n, double* d, double* e, double*
   }
   d[n - 1] = M.H(n - 1, n - 1);
   e[n - 1] = 0.0;
-  // Q = H_0 H_1 ... H_{n-3}, accumulated backwards in place: before H_k is applied the
-  // trailing block [k+1.., k+1..] holds H_{k+1} ... H_{n-3}; v_k sits in column k.
-  const int k0 = n >= 2 ? n - 2 : 0;
-  for (int i = k0; i < n; ++i)
-    for (int j = k0; j < n; ++j) M.H(i, j) = (i == j) ? 1.0 : 0.0;
-  for (int k = n - 3; k >= 0; --k) {
-    const int b = k + 1;
-    for (int j = b; j < n; ++j) {      // grow the block by row / column b, keeping v_k in column k
-      M.H(b, j) = (j == b) ? 1.0 : 0.0;
-      M.H(j, b) = (j == b) ? 1.0 : 0.0;
-    }
-    const double tk = tau[k];
-    if (tk != 0.0) {
-      for (int i = b; i < n; ++i) v[i] = M.H(i, k);
-      for (int j = b; j < n; ++j) p[j] = 0.0;
-      for (int i = b; i < n; ++i) {    // p_j = tk sum_i v_i Q_ij, row by row
-        const double vi = v[i];
-        for (int j = b; j < n; ++j) p[j] += vi * M.H(i, j);
-      }
-      for (int i = b; i < n; ++i) {
-        const double vi = tk * v[i];
-        for (int j = b; j < n; ++j) M.H(i, j) -= vi * p[j];
-      }
-    }
-  }
-  for (int j = 0; j < n; ++j) {        // row / column 0 of Q
-    M.H(0, j) = (j == 0) ? 1.0 : 0.0;
-    M.H(j, 0) = (j == 0) ? 1.0 : 0.0;
-  }
 }
 
 // Eigenvalues of the tridiagonal (d, e) by the implicit-shift QL method (Bowdler, Martin,
@@ -300,30 +272,36 @@ __device__ void lane_tri_vectors(const Lane& M, int n, const double* d, const do
   }
 }
 
-// C = L^{-T} Q Z, four columns at a time: first Q Z into Z (each block of four columns of Z read
-// into x4 before it is overwritten), then the back substitution with L^T into H.
+// C = L^{-T} Q Z in place of Z, four columns at a time: the reflectors of Q applied to the block
+// (H_{n-3} first), then the back substitution with L^T.
 template <int NUCAP>
-__device__ void lane_back_transform(const Lane& M, int n, const double* rdiag, double (*x4)[NUCAP]) {
+__device__ void lane_back_transform(const Lane& M, int n, const double* rdiag, const double* tau,
+                                    double (*x4)[NUCAP]) {
   for (int a0 = 0; a0 < n; a0 += 4) {
     const int na = min(4, n - a0);
     for (int r = 0; r < 4; ++r)
       for (int k = 0; k < n; ++k) x4[r][k] = r < na ? M.Z(k, a0 + r) : 0.0;
-    for (int i = 0; i < n; ++i) {
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int k = 0; k < n; ++k) {
-        const double q = M.H(i, k);
+    for (int k = n - 3; k >= 0; --k) {   // x <- (I - tau_k v_k v_k^T) x
+      const double tk = tau[k];
+      if (tk == 0.0) continue;
+      double dot[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int i = k + 1; i < n; ++i) {
+        const double vi = M.H(i, k);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) acc[r] += q * x4[r][k];
+        for (int r = 0; r < 4; ++r) dot[r] += vi * x4[r][i];
       }
-      for (int r = 0; r < na; ++r) M.Z(i, a0 + r) = acc[r];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) dot[r] *= tk;
+      for (int i = k + 1; i < n; ++i) {
+        const double vi = M.H(i, k);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) x4[r][i] -= dot[r] * vi;
+      }
     }
-  }
-  for (int a0 = 0; a0 < n; a0 += 4) {   // C = L^{-T} (Q Z), by columns, kept in x4
-    const int na = min(4, n - a0);
-    for (int i = n - 1; i >= 0; --i) {
+    for (int i = n - 1; i >= 0; --i) {   // C = L^{-T} (Q Z)
       double s[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) s[r] = r < na ? M.Z(i, a0 + r) : 0.0;
+      for (int r = 0; r < 4; ++r) s[r] = x4[r][i];
       for (int k = i + 1; k < n; ++k) {
         const double l = M.S(k, i);
 #pragma unroll
@@ -333,7 +311,7 @@ __device__ void lane_back_transform(const Lane& M, int n, const double* rdiag, d
       for (int r = 0; r < 4; ++r) x4[r][i] = s[r] * rdiag[i];
     }
     for (int r = 0; r < na; ++r)
-      for (int i = 0; i < n; ++i) M.H(i, a0 + r) = x4[r][i];
+      for (int i = 0; i < n; ++i) M.Z(i, a0 + r) = x4[r][i];
   }
 }
 
@@ -355,11 +333,11 @@ __global__ void __launch_bounds__(128) reduced_kernel(const RedArgs A) {
   if (ok) {
     lane_congruence(M, n, rdiag, v, p);
     lane_tridiag(M, n, d, e, p, tau, v);
-    for (int k = 0; k < n; ++k) {      // the eigenvalues from copies: T stays for the eigenvectors
-      p[k] = d[k];
-      tau[k] = e[k];
+    for (int k = 0; k < n; ++k) {      // the eigenvalues from copies: T stays for the eigenvectors,
+      p[k] = d[k];                     // tau for the back-transform
+      v[k] = e[k];
     }
-    ok = lane_tql_values(n, p, tau);
+    ok = lane_tql_values(n, p, v);
   }
   if (ok) {
     for (int a = 1; a < n; ++a) {      // ascending
@@ -369,7 +347,7 @@ __global__ void __launch_bounds__(128) reduced_kernel(const RedArgs A) {
       p[b + 1] = t;
     }
     lane_tri_vectors(M, n, d, e, p, v, x4[0], x4[1], x4[2], x4[3], rank);
-    lane_back_transform<NUCAP>(M, n, rdiag, x4);
+    lane_back_transform<NUCAP>(M, n, rdiag, tau, x4);
     for (int a = 0; a < n; ++a) {
       d[a] = p[a];
       rank[a] = a;
@@ -390,7 +368,7 @@ __global__ void __launch_bounds__(128) reduced_kernel(const RedArgs A) {
     for (int a = 0; a < n; ++a) {      // w_alpha = V_{j alpha} (S V)_{j alpha}
       double vj = 0.0, svj = 0.0;
       for (int k = 0; k < n; ++k) {
-        const double ck = M.H(k, a);
+        const double ck = M.Z(k, a);
         vj += M.UJ(k) * ck;
         svj += M.SUJ(k) * ck;
       }
@@ -406,12 +384,12 @@ __global__ void __launch_bounds__(128) reduced_kernel(const RedArgs A) {
     if (ok)
       for (int a = 0; a < ne; ++a) {      // V_j alpha = (row j of U) . c_alpha
         double v = 0.0;
-        for (int k = 0; k < ne; ++k) v += M.UJ(k) * M.H(k, a);
+        for (int k = 0; k < ne; ++k) v += M.UJ(k) * M.Z(k, a);
         e[a] = v;
       }
     for (int r = 0; r < nu; ++r)
       for (int a = 0; a < nu; ++a)
-        out[(size_t)(r * nu + a) * 32] = (r < ne && a < ne) ? M.H(r, inv[a]) : 0.0;
+        out[(size_t)(r * nu + a) * 32] = (r < ne && a < ne) ? M.Z(r, inv[a]) : 0.0;
     for (int a = 0; a < nu; ++a) out[(size_t)(nu * nu + a) * 32] = a < ne ? e[inv[a]] : 0.0;
   }
 }
