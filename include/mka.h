@@ -446,9 +446,10 @@ mka_status mka_autotune_batch(mka_system* sys, const mka_solve_params* prm, cons
  * = atoms [g chunk_atoms, (g+1) chunk_atoms) of the whole system) in a fixed
  * order, and the chunk sums are added in chunk order. Processes whose ranges
  * start on chunk boundaries therefore produce the very chunk sums a single
- * process over the whole system produces, and a bisection that adds them in
- * chunk order (mka_sweep_find_mu here, or a host driver over all processes'
- * mka_sweep_chunk_sums) finds the same mu, bit for bit. */
+ * process over the whole system produces, and a root finder that adds them in
+ * chunk order and takes the same steps (mka_sweep_find_mu here, or a host
+ * driver over all processes' mka_sweep_chunk_sums) finds the same mu, bit for
+ * bit. */
 typedef struct mka_sweep mka_sweep;
 
 /* A sweep over atoms [atom_begin, atom_end) of `sys` for subspaces of size nu
@@ -482,11 +483,17 @@ mka_status mka_sweep_status(mka_sweep* sw, int64_t* n_stored, int64_t* n_overflo
  * (host outputs); synchronises. MKA_ERR_INVALID_ARG when there is none. */
 mka_status mka_sweep_level_range(mka_sweep* sw, double* lo, double* hi);
 
-/* mu by bisection on 2 sum_j sum_alpha f(eps; mu) w = n_electrons over every
- * column of the range, all on the device: bracket [lo - 40 kT, hi + 40 kT]
- * from mka_sweep_level_range, halved while wider than `tol` (eV), at most 200
- * times; the count at each midpoint is the chunk-ordered sum above. Every atom
- * of the range must have been stored (MKA_ERR_INVALID_ARG otherwise). */
+/* mu with 2 sum_j sum_alpha f(eps; mu) w = n_electrons over every column of
+ * the range, all on the device, by a bracketing root finder: the bracket
+ * [lo - 40 kT, hi + 40 kT] from mka_sweep_level_range (the count is 0 at its
+ * lower end); its upper end evaluated first; bisection while the bracket is
+ * wider than 16 kT, then the secant through the bracket's ends (regula falsi
+ * with the Illinois rule), the midpoint when the secant leaves the bracket;
+ * a point where the count equals n_electrons exactly closes the bracket on
+ * it; until the bracket is no wider than `tol` (eV), at most 200 steps; mu =
+ * the bracket's midpoint. The count at each point is the chunk-ordered sum above,
+ * and every step uses IEEE-rounded operations only. Every atom of the range
+ * must have been stored (MKA_ERR_INVALID_ARG otherwise). */
 mka_status mka_sweep_find_mu(mka_sweep* sw, double n_electrons, double kT, double tol, double* mu);
 
 /* rho at mu into the caller's device buffer `rho` (double [n_blocks][4][4],

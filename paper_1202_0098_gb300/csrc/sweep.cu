@@ -36,9 +36,12 @@ constexpr int kChunkThreads = 256;
 constexpr int kRangeBlocks = 1024;
 constexpr int kMaxHalvings = 200;
 
+// The root finder's state: the bracket [lo, hi] with f = N - N_e at its ends, the next point x, the
+// side that moved last (-1 lo, +1 hi) and whether x came from the secant (rf).
 struct BisState {
-  double lo, hi, target, kT, tol, last, iters, pad;
+  double lo, hi, target, kT, tol, last, iters, x, flo, fhi, side, rf;
 };
+constexpr double kSecantKT = 16.0;   // bisection while the bracket is wider than this many kT
 
 __device__ __forceinline__ double fermi_f(double x, double mu, double r2kT) {   // r2kT = 1 / (2 kT)
   const double y = (x - mu) * r2kT;
@@ -230,7 +233,7 @@ struct ChunkArgs {
   int nu;
   int64_t a0, a1, chunk_atoms, chunk0;
   double mu;                 // used when S == NULL
-  const BisState* S;         // bisection: mu = midpoint of the bracket; nothing once converged
+  const BisState* S;         // root finder: mu = the state's next point; nothing once converged
   double kT;
   double* count;             // [n_chunks] 2 sum f w
   double* e_levels;          // [n_chunks] 2 sum f eps w (may be NULL)
@@ -243,7 +246,7 @@ __global__ void __launch_bounds__(kChunkThreads) sweep_chunk_kernel(const ChunkA
   double mu = A.mu, kT = A.kT;
   if (A.S) {
     if (!(A.S->hi - A.S->lo > A.S->tol)) return;
-    mu = 0.5 * (A.S->lo + A.S->hi);
+    mu = A.S->x;
     kT = A.S->kT;
   }
   const double r2kT = 0.5 / kT;        // one division per thread, a product per level
@@ -273,16 +276,51 @@ __global__ void __launch_bounds__(kChunkThreads) sweep_chunk_kernel(const ChunkA
   }
 }
 
-// One halving: the count at the midpoint is the chunk sums added in chunk order.
+// One step of the root finder for N(mu) = N_e: the count at x is the chunk sums added in chunk order;
+// the bracket end on its side moves to x. The next point is the midpoint while the bracket is wider
+// than 16 kT, then the secant through the ends (regula falsi, with the Illinois rule: after two moves
+// of the same end by the secant, the other end's f is halved), the midpoint when the secant leaves the
+// bracket; a point where the count equals N_e exactly closes the bracket on it. IEEE-rounded
+// operations throughout (no contraction), so that a host driver doing the same
+// arithmetic on the same chunk sums takes the same points bit for bit.
 __global__ void sweep_bisect_step_kernel(const double* count, int64_t n_chunks, BisState* S) {
   if (!(S->hi - S->lo > S->tol)) return;
-  const double mid = 0.5 * (S->lo + S->hi);
   double t = 0.0;
   for (int64_t k = 0; k < n_chunks; ++k) t += count[k];
-  if (t < S->target) S->lo = mid;
-  else S->hi = mid;
+  const double x = S->x, fx = __dsub_rn(t, S->target);
+  if (fx == 0.0) {                     // x is a root to rounding: the bracket closes on it
+    S->lo = x;
+    S->hi = x;
+    S->flo = 0.0;
+    S->fhi = 0.0;
+    S->last = t;
+    S->iters += 1;
+    return;
+  }
+  if (fx < 0.0) {
+    S->lo = x;
+    S->flo = fx;
+    if (S->rf != 0.0 && S->side == -1.0) S->fhi = __dmul_rn(0.5, S->fhi);
+    S->side = -1.0;
+  } else {
+    S->hi = x;
+    S->fhi = fx;
+    if (S->rf != 0.0 && S->side == 1.0) S->flo = __dmul_rn(0.5, S->flo);
+    S->side = 1.0;
+  }
   S->last = t;
   S->iters += 1;
+  const double lo = S->lo, hi = S->hi, mid = __dmul_rn(0.5, __dadd_rn(lo, hi));
+  double nx = mid, rf = 0.0;
+  if (!(__dsub_rn(hi, lo) > __dmul_rn(kSecantKT, S->kT))) {
+    const double sx = __ddiv_rn(__dsub_rn(__dmul_rn(lo, S->fhi), __dmul_rn(hi, S->flo)), __dsub_rn(S->fhi, S->flo));
+    if (lo < sx && sx < hi) {
+      nx = sx;
+      rf = 1.0;
+    }
+  }
+  S->x = nx;
+  S->rf = rf;
 }
 
 struct RhoArgs {
@@ -712,10 +750,16 @@ mka_status mka_sweep_find_mu(mka_sweep* sw, double n_electrons, double kT, doubl
   h.target = n_electrons;
   h.kT = kT;
   h.tol = tol;
+  h.x = h.hi;                 // first point: every level occupied (N(lo) = 0 needs no pass)
+  h.flo = -n_electrons;
+  h.fhi = 0.0;
+  h.side = 0.0;
+  h.rf = 0.0;
   cudaStream_t st = sw->stream;
   MKA_CUDA_TRY(cudaMemcpyAsync(sw->d_state, &h, sizeof(h), cudaMemcpyHostToDevice, st));
   for (int i = 0; i < kMaxHalvings; ++i) {
-    // both kernels return at once when the bracket is already narrower than tol
+    // both kernels return at once when the bracket is already narrower than tol (the loop's bound is
+    // the bisection's worst case; the secant phase usually ends it after a few steps)
     s = chunk_launch(sw, 0.0, kT, sw->d_state, false, false);
     if (s) return s;
     sweep_bisect_step_kernel<<<1, 1, 0, st>>>(sw->d_chunk, sw->n_chunks, sw->d_state);

@@ -79,24 +79,49 @@ def gather_chunks(parts, n_chunks_total: int, key: str, mu: float, kT: float, gr
     return _all_reduce(full, "sum", group, device)
 
 
+SECANT_KT = 16.0   # bisection while the bracket is wider than this many kT, then the secant
+
+
 def find_mu(parts, n_chunks_total: int, n_electrons: float, kT: float, tol: float = 1e-12, group=None,
             device="cpu") -> tuple[float, int]:
-    """mu by bisection on the electron count of every column of all processes; (mu, halvings).
+    """mu with N(mu) = n_electrons over every column of all processes; (mu, steps).
 
-    Bracket [min eps - 40 kT, max eps + 40 kT] over levels with nonzero weight; each halving takes the
-    count at the midpoint as the chunk-ordered sum, the upper half when it falls short of n_electrons."""
+    The library's root finder step for step (mka_sweep_find_mu): bracket [min eps - 40 kT, max eps + 40 kT]
+    over levels with nonzero weight (N = 0 at its lower end), its upper end evaluated first, bisection
+    while the bracket is wider than 16 kT, then regula falsi with the Illinois rule (after two moves of the
+    same end by the secant the other end's f is halved), the midpoint when the secant leaves the bracket;
+    the count at each point is the chunk-ordered sum; a point where it equals n_electrons exactly closes
+    the bracket on it; mu = the bracket's midpoint once it is no wider than tol. Python floats round like
+    the device's IEEE operations, so the points agree bit for bit."""
     rng = np.array([[*p.level_range()] for p in parts])
     lo = float(_all_reduce(np.array([rng[:, 0].min()]), "min", group, device)[0]) - 40.0 * kT
     hi = float(_all_reduce(np.array([rng[:, 1].max()]), "max", group, device)[0]) + 40.0 * kT
+    flo, fhi, side, rf = -float(n_electrons), 0.0, 0, False
+    x = hi
     it = 0
     while it < MAX_HALVINGS and hi - lo > tol:
-        mid = 0.5 * (lo + hi)
-        t = _ordered_sum(gather_chunks(parts, n_chunks_total, "count", mid, kT, group, device))
-        if t < n_electrons:
-            lo = mid
+        t = _ordered_sum(gather_chunks(parts, n_chunks_total, "count", x, kT, group, device))
+        fx = t - n_electrons
+        if fx == 0.0:                  # x is a root to rounding: the bracket closes on it
+            lo = hi = x
+            it += 1
+            break
+        if fx < 0:
+            lo, flo = x, fx
+            if rf and side == -1:
+                fhi = 0.5 * fhi
+            side = -1
         else:
-            hi = mid
+            hi, fhi = x, fx
+            if rf and side == 1:
+                flo = 0.5 * flo
+            side = 1
         it += 1
+        x, rf = 0.5 * (lo + hi), False
+        if not (hi - lo > SECANT_KT * kT):
+            sx = (lo * fhi - hi * flo) / (fhi - flo)
+            if lo < sx < hi:
+                x, rf = sx, True
     return 0.5 * (lo + hi), it
 
 
