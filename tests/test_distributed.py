@@ -132,3 +132,29 @@ def test_gloo_ranks_reproduce_single_process(tmp_path, world):
         got = np.load(tmp_path / f"r{r}.npy")
         assert got[0] == mu1 and got[1] == it1
         assert got[2] == t1["n_electrons"] and got[3] == t1["e_band_levels"]
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_root_finder_agrees_with_bisection(seed):
+    """The whole-system root finder (bisection while the bracket is wider than 16 kT, then the Illinois
+    secant; the library's device loop takes the same steps) against the oracle's plain bisection on random
+    level sets with kT from 0.01 to 0.5 eV, fillings from 10 to 90 % and (every third set) levels rounded
+    to 0.1 eV so that many coincide. mu agrees within 1e-9 eV plus what the rounding of the electron count
+    allows: where N(mu) is nearly flat (mu in a gap, small kT) any root finder is fixed only to
+    (noise in N) / (dN/dmu), with dN/dmu = sum 2 w f (1 - f) / kT at the oracle's mu. The secant needs far
+    fewer passes than bisection's ~46."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(8, 200))
+    kT = float(rng.choice([0.01, 0.05, 0.1, 0.5]))
+    eps, w = seeded_levels(n, seed=100 + seed)
+    if seed % 3 == 0:
+        eps = np.round(eps, 1)
+    n_e = 8.0 * n * float(rng.uniform(0.1, 0.9))
+    n_chunks = (n + CHUNK - 1) // CHUNK
+    mu, it = D.find_mu([ArrayPart(eps, w, 0, n)], n_chunks, n_e, kT)
+    mu_o = omka.find_mu(eps, w, n_e, kT)
+    f = omka.fermi(eps.ravel(), mu_o, kT)
+    slope = float(np.sum(2.0 * w.ravel() * f * (1.0 - f))) / kT
+    noise = 1e-12 * n_e
+    assert abs(mu - mu_o) <= 1e-9 + (noise / slope if slope > 0 else np.inf), (n, kT, mu, mu_o, slope)
+    assert it <= 40, it
