@@ -50,10 +50,10 @@ class SweepPart:
 
 def _all_reduce(values: np.ndarray, op: str, group, device) -> np.ndarray:
     """Reduce over the processes of `group` (None: this process alone)."""
-    import torch.distributed as dist
-    if group is None and not (dist.is_available() and dist.is_initialized()):
+    if group is None:
         return values
     import torch
+    import torch.distributed as dist
     t = torch.from_numpy(np.ascontiguousarray(values, dtype=np.float64)).to(device)
     dist.all_reduce(t, op={"sum": dist.ReduceOp.SUM, "min": dist.ReduceOp.MIN, "max": dist.ReduceOp.MAX}[op],
                     group=group)
