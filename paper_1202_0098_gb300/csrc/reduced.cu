@@ -3,11 +3,11 @@
 // Every column j ends its basis with the nu x nu projected matrices H_r = U^T H U and
 // S_r = U^T S U (formed explicitly, so that a basis that is only nearly S-orthonormal
 // still gives the Galerkin pencil of its span) and solves the generalized eigenproblem
-// H_r c = eps S_r c (Eq. EQ-SUB-EIG-VEC): Cholesky S_r = L L^T, A = L^{-1} H_r L^{-T} (lower triangle),
-// Householder tridiagonalisation A = Q T Q^T, the eigenvalues of T by the implicit-shift QL
-// method, the eigenvectors Z of T by inverse iteration (re-orthogonalised within clusters of
-// close eigenvalues), C = L^{-T} Q Z with Q applied as its reflectors. The outputs of a column are its levels eps_alpha
-// in ascending order, w_alpha = V_{j alpha} (S V)_{j alpha} with V = U C (Eq. EQ-DM's
+// H_r c = eps S_r c (Eq. EQ-SUB-EIG-VEC): Cholesky S_r = L L^T, A = L^{-1} H_r L^{-T} (lower
+// triangle), Householder tridiagonalisation A = Q T Q^T, the eigenvalues of T by the
+// implicit-shift QL method, the eigenvectors Z of T by inverse iteration (re-orthogonalised
+// within clusters of close eigenvalues), C = L^{-T} Q Z with Q applied as its reflectors. The
+// outputs of a column are its levels eps_alpha in ascending order, w_alpha = V_{j alpha} (S V)_{j alpha} with V = U C (Eq. EQ-DM's
 // weights), and, when vectors are kept, C and the row V_j = (row j of U) C in the same order:
 // rho_ij = sum_alpha f_alpha V_i alpha V_j alpha = U_i . (C diag(f) V_j) and G_ij(z) likewise,
 // so the kept pattern rows of U never need turning into rows of V.
@@ -42,8 +42,9 @@ struct RedArgs {
   int64_t col0;
 };
 
-// Element (i, j) of the lane's matrices: H_r / A / Q / C at (i nu + j), S_r / L at nu^2 + (i nu + j),
-// then row j of U and of S U, then the eigenvectors Z of T (and Q Z) at 2 nu^2 + 2 nu + (i nu + j).
+// Element (i, j) of the lane's matrices: H_r, then X = L^{-1} H_r (upper triangle) and A (lower
+// triangle), then Q's reflectors (below the diagonal) at (i nu + j); S_r / L at nu^2 + (i nu + j);
+// row j of U and of S U; the eigenvectors Z of T, then C, at 2 nu^2 + 2 nu + (i nu + j).
 struct Lane {
   double* b;
   int nu;
