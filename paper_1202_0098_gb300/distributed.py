@@ -7,7 +7,7 @@ need only small exchanges, all of vectors of chunk sums that the library compute
 (``mka_sweep_chunk_sums``):
 
 * the level range, once (min / max of the processes' ranges);
-* one sum of the chunk-count vector per bisection halving (Sec. 2: mu from the total
+* one sum of the chunk-count vector per root-finder step (Sec. 2: mu from the total
   electron number of all columns);
 * the chunk vectors of the electron count and band energy at the final mu.
 
@@ -16,9 +16,9 @@ exactly one process, from the same entries in the same order as a single process
 the whole system would; the zero-padded vectors' sum over processes is therefore exact,
 and adding it in chunk order reproduces the single-process mu and energies bit for bit.
 
-This module only orchestrates: it compares a sum with the target and halves a bracket,
-the way ``mka_sweep_find_mu`` does on one device; every sum over levels runs in the
-library's kernels.
+This module only orchestrates: it compares a sum with the target and narrows a bracket
+(bisection, then the Illinois secant), step for step as ``mka_sweep_find_mu`` does on one
+device; every sum over levels runs in the library's kernels.
 """
 from __future__ import annotations
 
@@ -61,7 +61,7 @@ def _all_reduce(values: np.ndarray, op: str, group, device) -> np.ndarray:
 
 
 def _ordered_sum(v: np.ndarray) -> float:
-    """Left-to-right sum, the order the device bisection adds its chunk sums in."""
+    """Left-to-right sum, the order the device root finder adds its chunk sums in."""
     t = 0.0
     for x in v.tolist():
         t += x

@@ -1,7 +1,7 @@
 """The multi-process data plane of the whole-system work flow, on CPU ranks (gloo).
 
 Each rank owns one chunk-aligned range of atoms; the only exchanges are the level range,
-one all-reduce of the chunk-count vector per bisection halving, and the final chunk
+one all-reduce of the chunk-count vector per root-finder step, and the final chunk
 vectors (`paper_1202_0098_gb300.distributed`). The per-chunk sums here are a numpy
 stand-in for the library's chunk kernel (the oracle's Fermi function over a chunk's
 entries in a fixed order): what is tested is the host logic — ranges, the zero-padded
